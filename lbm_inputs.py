@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+Shared by the CUDA path (bench, tests) and by the oracle.  It holds none of
+the method's arithmetic: only random initial fields and the workload
+definitions, whose parameters are plain numbers (physical inputs where the
+paper derives lattice values from them; each side converts them with its own
+similarity helper).
+
+Node index is x + nx*(y + ny*z); vector fields have shape (D, N).
+"""
+import numpy as np
+
+CS2_PK = 1.0 / 3.0  # kinematic pressure of the reference state (eps_g = 1)
+
+# Boundary codes (same meaning on both sides).
+PERIODIC, WALL, INLET, OUTLET = 0, 1, 2, 3
+
+# Physical inputs of the drag relation used by the workloads (Sec. 3.6, TEST #4):
+# drag coefficient, gravity, lattice speed.
+C_D = 0.66
+G_PHYS = 9.81
+C_LATTICE = 69.2
+
+
+def _common_physics(R=1000.0):
+    """R = 1000, dynamic viscosity ratio 50 (nu_g = 20 nu_l), CGW drag with a
+    1 mm dispersed diameter, (R-1) g_hat = 1e-6, stabilisers gamma = 1,
+    n_gamma = 200 (the settings of TEST #3/#4)."""
+    return dict(
+        R=R, omega_g=0.6, nu_ratio_g_over_l=20.0, omega_alpha=1.5, psi_g=0.0, psi_l=0.0,
+        drag_model=1, d_m=1.0e-3, C_d=C_D, g_phys=G_PHYS, c_lattice=C_LATTICE,
+        g_hat=1.0e-6 / (R - 1.0), gamma=1.0, n_gamma=200, spalding_mode=2, alpha_floor=1e-8,
+    )
+
+
+WORKLOADS = {
+    # 1D gas-liquid column, D1Q3, FP64, walls at both ends, gravity along x.
+    "column1d": dict(
+        lattice="D1Q3", dims=(512, 1, 1), steps=10000, precision="fp64",
+        physics=dict(_common_physics(), wall_friction=True, g_axis=0,
+                     bc_lo=(WALL, 0, 0), bc_hi=(WALL, 0, 0)),
+    ),
+    # 2D bubble-column box, D2Q9, FP32, periodic x, walls y, bottom inlet strip.
+    "box2d": dict(
+        lattice="D2Q9", dims=(512, 2048, 1), steps=20000, precision="fp32",
+        physics=dict(_common_physics(), wall_friction=False, g_axis=1,
+                     bc_lo=(PERIODIC, INLET, 0), bc_hi=(PERIODIC, WALL, 0),
+                     inlet_lo=192, inlet_hi=320, in_alpha=(0.01, 0.3), in_ug=(4.3e-4, 4.3e-3),
+                     in_ul=(0.0, 0.0), inlet_ul_mode=1, ramp_nt=1667),
+    ),
+    # 3D column, D3Q19, walls on the four x/y faces, periodic z, gravity along z.
+    "column3d": dict(
+        lattice="D3Q19", dims=(256, 256, 512), steps=5000, precision="fp16dev",
+        physics=dict(_common_physics(), wall_friction=False, g_axis=2,
+                     bc_lo=(WALL, WALL, PERIODIC), bc_hi=(WALL, WALL, PERIODIC)),
+    ),
+}
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def fields_column1d(n=512, seed=1):
+    """alpha_g = 0.9 below mid-column, 0.1 above, plus U(-1e-3, 1e-3), clipped to
+    [0.01, 0.99]; both phases at rest; p_k at the reference value."""
+    r = rng(seed)
+    a = np.where(np.arange(n) < n // 2, 0.9, 0.1) + r.uniform(-1e-3, 1e-3, n)
+    a = np.clip(a, 0.01, 0.99)
+    z = np.zeros((1, n))
+    return dict(alpha_g=a, u_g=z.copy(), u_l=z.copy(), p_k=np.full(n, CS2_PK))
+
+
+def fields_box2d(nx=512, ny=2048, seed=2, alpha0=0.01, u_noise=4.3e-5):
+    """Background alpha_g = 0.01; every velocity component of both phases is
+    U(-1, 1) * 1 % of the maximum inlet gas velocity."""
+    r = rng(seed)
+    n = nx * ny
+    return dict(alpha_g=np.full(n, alpha0),
+                u_g=r.uniform(-1.0, 1.0, (2, n)) * u_noise,
+                u_l=r.uniform(-1.0, 1.0, (2, n)) * u_noise,
+                p_k=np.full(n, CS2_PK))
+
+
+def fields_column3d(nx=256, ny=256, nz=512, seed=3, mean=0.05, std=0.01, corr=8.0):
+    """alpha_g = mean + std * (white noise smoothed by a Gaussian of standard
+    deviation `corr` nodes, periodic FFT filter, re-standardised); at rest."""
+    r = rng(seed)
+    noise = r.standard_normal((nz, ny, nx))
+    k = [np.fft.fftfreq(m) for m in (nz, ny, nx)]
+    kz, ky, kx = np.meshgrid(*k, indexing="ij")
+    filt = np.exp(-2.0 * (np.pi * corr) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    sm = np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    sm = (sm - sm.mean()) / sm.std()
+    a = np.clip(mean + std * sm, 0.01, 0.99).reshape(-1)
+    n = nx * ny * nz
+    z = np.zeros((3, n))
+    return dict(alpha_g=a, u_g=z.copy(), u_l=z.copy(), p_k=np.full(n, CS2_PK))
+
+
+def fields_random(D, dims, seed, alpha=(0.2, 0.8), u_amp=2e-3, pk_amp=1e-4):
+    """Generic random smooth-ish state for parity tests: alpha_g uniform in
+    `alpha`, velocities uniform in +-u_amp, p_k = 1/3 + uniform +-pk_amp."""
+    r = rng(seed)
+    n = int(np.prod(dims))
+    return dict(alpha_g=r.uniform(alpha[0], alpha[1], n),
+                u_g=r.uniform(-u_amp, u_amp, (D, n)),
+                u_l=r.uniform(-u_amp, u_amp, (D, n)),
+                p_k=CS2_PK + r.uniform(-pk_amp, pk_amp, n))
+
+
+def fields_for(name, dims=None, seed=None):
+    w = WORKLOADS[name]
+    dims = dims or w["dims"]
+    if name == "column1d":
+        return fields_column1d(dims[0], seed if seed is not None else 1)
+    if name == "box2d":
+        return fields_box2d(dims[0], dims[1], seed if seed is not None else 2)
+    if name == "column3d":
+        return fields_column3d(dims[0], dims[1], dims[2], seed if seed is not None else 3)
+    raise KeyError(name)
