@@ -1,0 +1,169 @@
+/*
+ * lbm.h -- C ABI of the GB300 library for the six coupled lattice Boltzmann
+ * schemes of the Eulerian-Eulerian multiphase framework of Piredda & Asinari
+ * (arXiv 2409.10399): f_g, f_l (artificially compressible phase momenta,
+ * Sec. 2.1.1), f_alpha_g, f_alpha_l (volume fractions, Sec. 2.2) and f_beta_g,
+ * f_beta_l (continuity sources, Sec. 2.3), on one D1Q3, D2Q9 or D3Q19 lattice.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status: LBM_OK (0) or a negative LBM_E*
+ *    code.  Nothing aborts or exits.  lbm_last_error() gives a one-line text.
+ *  - Lattice units (hatted quantities of the paper).  Node index
+ *    i = x + nx*(y + ny*z); a vector field is D consecutive planes of N nodes
+ *    (SoA), D = 1, 2, 3 for D1Q3, D2Q9, D3Q19.
+ *  - Buffers passed in are owned by the caller; the library copies from/to
+ *    them during the call (or on the context's stream for on_device = 1) and
+ *    never keeps a pointer.  `on_device` = 1 means the pointers are CUDA
+ *    device pointers of the current device, 0 means host memory.
+ *  - The library owns the population store (6*Q planes in HBM) and all
+ *    scratch.  Work is enqueued on the context's stream (default: the legacy
+ *    default stream; see lbm_set_stream).
+ *  - Errors are sticky: after LBM_ENAN or LBM_EDRIFT, lbm_step returns
+ *    LBM_ESTATE until the next lbm_init.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,   /* bad argument: sizes, rates, boundary codes, NULL */
+  LBM_ENOMEM = -2,   /* device allocation failed */
+  LBM_ECUDA = -3,    /* a CUDA call failed (text in lbm_last_error) */
+  LBM_ENAN = -4,     /* diagnostics found a non-finite population */
+  LBM_EDRIFT = -5,   /* per-phase volume drifted beyond drift_limit */
+  LBM_ETIMEOUT = -6, /* a bounded wait ran out */
+  LBM_ESTATE = -7    /* call out of order (not initialised, sticky error) */
+};
+
+enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2, LBM_D3Q19 = 3 };
+
+/* Storage/arithmetic of the populations.  FP64: double store and math.
+ * FP32: float store of the deviations f - w_q*r_s and float math.
+ * FP16DEV: half store of the same deviations, float math. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2 };
+
+/* Face conditions.  WALL: half-way bounce-back for all six schemes (Eq.
+ * (BCINLET), BB rule with zero wall velocity).  INLET: Table 1, only on the
+ * low face of g_axis, inside the strip [inlet_lo, inlet_hi) of the first
+ * transverse axis (a wall elsewhere on that face; the whole face in 1D).
+ * OUTLET: Table 2, only on the high face of g_axis. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INLET = 2, LBM_BC_OUTLET = 3 };
+
+/* K_I = kappa_I (CONST) or K_I = kappa_I * Lambda' with Lambda of Eq. (Lambda)
+ * (Clift-Grace-Weber, Eq. (CliftGraceWeber)); the liquid wall friction of
+ * Eq. (wallmomentum1D) uses kappa_W the same way and is active when
+ * kappa_W != 0. */
+enum { LBM_DRAG_CONST = 0, LBM_DRAG_CGW = 1 };
+
+typedef struct {
+  double R;                  /* rho_l / rho_g >= 1, Eq. (lbm-phi-l) */
+  double omega_g, omega_l;   /* BGK rates of f_g, f_l in (0,2), Eq. (colloperator) */
+  double omega_alpha;        /* rate of f_alpha in (0,2), Eq. (lbmalpha) */
+  double psi_g, psi_l;       /* forcing knob of Eq. (forcingoperator); 0 = the
+                                paper's choice xi = 5/3 nu (Sec. 3.5) */
+  int drag_model;            /* LBM_DRAG_* */
+  double kappa_I, kappa_W;
+  double g_hat;              /* buoyancy (R-1)*g_hat on the gas along +g_axis,
+                                kinematic-pressure form, Eq. (Gg1D) */
+  int g_axis;                /* 0, 1, 2 < D */
+  double gamma;              /* Ohwada dashpot, Eqs. (lbm-cont-g1Dhat), (lbm-cont-l1Dhat) */
+  int n_gamma;               /* >= 1: S'' and Lambda' latched when t % n_gamma == 0,
+                                Eqs. (lbm-cont-1D-update), (Lambda-update) */
+  int spalding_mode;         /* 0 off; 1 alpha^B in couplings only; 2 alpha^B also
+                                in the f_alpha equilibrium (Eq. (spalding)) */
+  double alpha_floor;        /* floor of alpha in the 1/alpha factors (> 0) */
+  int bc_lo[3], bc_hi[3];    /* LBM_BC_* per axis face; unused axes ignored */
+  int inlet_lo, inlet_hi;    /* inlet strip on the first transverse axis */
+  double in_alpha[2];        /* (min, max) of alpha_g^IN, ramp Eq. (transient) */
+  double in_ug[2];           /* (min, max) of u_g^IN along +g_axis */
+  double in_ul[2];           /* (min, max) of u_l^IN (inlet_ul_mode 0) */
+  int ramp_nt;               /* n_t of Eq. (transient); <= 0: the max at once */
+  int inlet_ul_mode;         /* 0: u_l^IN ramp; 1: u_l^IN = -a u_g^IN/(1-a)
+                                (zero net volume flux through the strip) */
+  int precision;             /* LBM_FP64 / LBM_FP32 / LBM_FP16DEV */
+  int diag_every;            /* > 0: FP64 diagnostics every that many steps
+                                inside lbm_step, checked for NaN / drift */
+  double drift_limit;        /* relative drift of sum(a_g) that raises
+                                LBM_EDRIFT (closed domains only); <= 0: off */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+/* Fill `p` with the defaults (R = 2, omega = 1, omega_alpha = 1.5, psi = 0,
+ * CONST drag 0, no gravity, gamma = 0, n_gamma = 1, Spalding mode 2,
+ * alpha_floor = 1e-8, all faces periodic, FP32, no diagnostics). */
+void lbm_default_params(lbm_params *p);
+
+/* Allocate a simulation of one lattice.  dim must equal the lattice's D
+ * (ny = nz = 1 for D1Q3, nz = 1 for D2Q9).  Validates rates, sizes and
+ * boundary codes (LBM_EINVAL), allocates 6*Q*N populations plus three held
+ * fields (S''_g, S''_l, Lambda') and small scratch on the current CUDA device
+ * (LBM_ENOMEM).  *out is NULL on failure. */
+int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p, lbm_ctx **out);
+
+/* Set every scheme to its equilibrium from macroscopic fields and reset t = 0:
+ * f_g = f_I^eq(1, eps_g, u_g) with eps_g = p_k/cs2 (Eq. (sigmag1D)),
+ * f_l = f_I^eq(phi, 1, u_l) with phi of Eq. (lbm-phi-l), f_alpha = f^eq(alpha, u)
+ * with alpha_l = 1 - alpha_g, f_beta = f^eq(1, c) with c of Eq. (velocitybeta);
+ * S'' = 0, Lambda' = Lambda(alpha_g).  alpha_g, p_k: N doubles; u_g, u_l:
+ * D*N doubles.  Clears sticky errors. */
+int lbm_init(lbm_ctx *c, const double *alpha_g, const double *u_g, const double *u_l,
+             const double *p_k, int on_device);
+
+/* Enqueue n fused collide-and-stream steps (n >= 0) on the context stream:
+ * moments, sources, Spalding, coupling, dashpot, lag, grad(alpha), stress,
+ * drag, forces, the six BGK/LKS collisions and AA-pattern in-place streaming
+ * with the face conditions (Sec. 2-3).  Returns after enqueueing; with
+ * diag_every > 0 it also checks the diagnostics it has already received
+ * (LBM_ENAN, LBM_EDRIFT).  LBM_ESTATE before lbm_init or after a sticky
+ * error. */
+int lbm_step(lbm_ctx *c, int n);
+
+/* Macroscopic fields of the current state (as the next step sees them), in
+ * FP64: alpha_g^B (Eq. (spalding)), u_g, u_l (D*N each), p_k = cs2*eps_g,
+ * S_g, S_l = 1 - beta (Eq. (lbmbetataylorzeroth5)).  Any pointer may be NULL.
+ * Synchronises the context stream before returning. */
+int lbm_get_moments(lbm_ctx *c, double *alpha_g, double *u_g, double *u_l, double *p_k,
+                    double *S_g, double *S_l, int on_device);
+
+/* Populations of scheme s (0 g, 1 l, 2 alpha_g, 3 alpha_l, 4 beta_g, 5 beta_l)
+ * as full values f (not deviations) in FP64, q-major: out[q*N + i], with the
+ * velocity order of lbm_lattice().  Synchronises. */
+int lbm_get_populations(lbm_ctx *c, int s, double *out, int on_device);
+
+/* Velocity set of lattice LBM_D1Q3/D2Q9/D3Q19 in the library's order:
+ * v[3*q + a] (a < 3, zero-padded), w[q]; returns Q through *Q.  Host
+ * pointers of length >= 3*19 and 19 (v or w may be NULL).  Needs no GPU. */
+int lbm_lattice(int lattice, int *Q, int *v, double *w);
+
+/* FP64 diagnostics of the current state (warp/block/grid reduction on the
+ * GPU): [0] sum a_g, [1] sum a_l, [2] sum alpha_g^B, [3] sum (a_g+a_l-1)^2,
+ * [4] max |u| over both phases, [5] number of nodes with a non-finite
+ * population, [6] sum (eps_g - 1), [7] sum (eps_l - 1).  Synchronises. */
+int lbm_get_diag(lbm_ctx *c, double out[8]);
+
+/* Use `cuda_stream` (a cudaStream_t of the current device, e.g. the value of
+ * torch.cuda.current_stream().cuda_stream) for all later work; NULL selects
+ * the legacy default stream.  The caller keeps the stream alive. */
+int lbm_set_stream(lbm_ctx *c, void *cuda_stream);
+
+/* Time step counter t (number of completed steps since lbm_init). */
+int lbm_time(const lbm_ctx *c, long long *t);
+
+/* Number of GPU kernel launches this context has issued since creation. */
+int lbm_launch_count(const lbm_ctx *c, long long *n);
+
+/* Text of the last error of this context ("" if none); NULL-safe. */
+const char *lbm_last_error(const lbm_ctx *c);
+
+/* Free the context and its device memory (synchronises); NULL-safe. */
+int lbm_destroy(lbm_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

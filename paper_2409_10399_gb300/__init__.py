@@ -1,0 +1,254 @@
+"""GB300 library of the six coupled Eulerian-Eulerian LBM schemes
+(Piredda & Asinari, arXiv 2409.10399), Python binding.
+
+The compute path is the CUDA library ``_build/liblbm.so`` behind the C ABI of
+``include/lbm.h``; this module only marshals arguments (numpy host arrays or
+torch CUDA tensors) into it.  There is no CPU fallback: if the library is not
+built, or no GPU is present, the calls raise.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Simulation", "LBMError", "load_library", "lattice_tables", "PRECISION", "LATTICE", "BC"]
+
+LATTICE = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2}
+BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
+ERRORS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ENAN",
+          -5: "LBM_EDRIFT", -6: "LBM_ETIMEOUT", -7: "LBM_ESTATE"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERRORS.get(code, "?"), code, (": " + msg) if msg else ""))
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``lbm_params`` (include/lbm.h)."""
+    _fields_ = [
+        ("R", ctypes.c_double),
+        ("omega_g", ctypes.c_double), ("omega_l", ctypes.c_double),
+        ("omega_alpha", ctypes.c_double),
+        ("psi_g", ctypes.c_double), ("psi_l", ctypes.c_double),
+        ("drag_model", ctypes.c_int), ("kappa_I", ctypes.c_double), ("kappa_W", ctypes.c_double),
+        ("g_hat", ctypes.c_double), ("g_axis", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("n_gamma", ctypes.c_int),
+        ("spalding_mode", ctypes.c_int), ("alpha_floor", ctypes.c_double),
+        ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
+        ("inlet_lo", ctypes.c_int), ("inlet_hi", ctypes.c_int),
+        ("in_alpha", ctypes.c_double * 2), ("in_ug", ctypes.c_double * 2), ("in_ul", ctypes.c_double * 2),
+        ("ramp_nt", ctypes.c_int), ("inlet_ul_mode", ctypes.c_int),
+        ("precision", ctypes.c_int), ("diag_every", ctypes.c_int), ("drift_limit", ctypes.c_double),
+    ]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def load_library(build_if_missing=True):
+    """Load liblbm.so (building it with nvcc if it is missing or stale)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        so = _build.SO
+        if build_if_missing:
+            so = _build.build()
+        if not os.path.exists(so):
+            raise RuntimeError("liblbm.so is not built; run paper_2409_10399_gb300.build.build()")
+        lib = ctypes.CDLL(so)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        dp = ctypes.c_void_p  # double* (host or device address)
+        sigs = {
+            "lbm_default_params": (None, [ctypes.POINTER(Params)]),
+            "lbm_lattice": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "lbm_create": (I, [I, I, I, I, I, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+            "lbm_init": (I, [P, dp, dp, dp, dp, I]),
+            "lbm_step": (I, [P, I]),
+            "lbm_get_moments": (I, [P, dp, dp, dp, dp, dp, dp, I]),
+            "lbm_get_populations": (I, [P, I, dp, I]),
+            "lbm_get_diag": (I, [P, ctypes.POINTER(D)]),
+            "lbm_set_stream": (I, [P, P]),
+            "lbm_time": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_last_error": (ctypes.c_char_p, [P]),
+            "lbm_destroy": (I, [P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def lattice_tables(lattice):
+    """(v[Q, D], w[Q]) of the library's velocity order (no GPU needed)."""
+    lib = load_library()
+    L = LATTICE[lattice]
+    Q = ctypes.c_int()
+    v = (ctypes.c_int * 57)()
+    w = (ctypes.c_double * 19)()
+    rc = lib.lbm_lattice(L, ctypes.byref(Q), v, w)
+    if rc:
+        raise LBMError(rc)
+    q = Q.value
+    return np.array(v[:3 * q], np.int64).reshape(q, 3)[:, :L], np.array(w[:q])
+
+
+def default_params():
+    p = Params()
+    load_library().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(d):
+    p = default_params()
+    for k, v in d.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if not hasattr(p, k):
+            continue
+        cur = getattr(p, k)
+        if isinstance(cur, ctypes.Array):
+            arr = type(cur)(*v)
+            setattr(p, k, arr)
+        elif isinstance(cur, int):
+            setattr(p, k, int(v))
+        else:
+            setattr(p, k, float(v))
+    return p
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Simulation:
+    """One lattice run on the current CUDA device.
+
+    ``Simulation("D2Q9", (nx, ny), params)`` where ``params`` is a dict of
+    ``lbm_params`` fields (``precision`` may be "fp64", "fp32", "fp16dev").
+    """
+
+    def __init__(self, lattice, dims, params):
+        self._lib = load_library()
+        self.lattice = lattice
+        self.D = LATTICE[lattice]
+        dims = tuple(int(d) for d in dims) + (1,) * (3 - len(dims))
+        self.dims = dims
+        self.N = dims[0] * dims[1] * dims[2]
+        self.params = make_params(params)
+        h = ctypes.c_void_p()
+        rc = self._lib.lbm_create(self.D, self.D, dims[0], dims[1], dims[2], ctypes.byref(self.params), ctypes.byref(h))
+        if rc:
+            raise LBMError(rc, "lbm_create(%s, %r)" % (lattice, dims))
+        self._h = h
+        self._stream = None
+
+    def _check(self, rc, what):
+        if rc:
+            msg = self._lib.lbm_last_error(self._h)
+            raise LBMError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """Use a torch.cuda.Stream (or a raw cudaStream_t int) for all work."""
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self._stream = stream
+        self._check(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(handle)), "lbm_set_stream")
+
+    def init(self, alpha_g, u_g, u_l, p_k):
+        """Fields as numpy float64 (host) or torch float64 CUDA tensors."""
+        arrs = [alpha_g, u_g, u_l, p_k]
+        if all(_is_torch(a) and a.is_cuda for a in arrs):
+            arrs = [a.contiguous() for a in arrs]
+            for a in arrs:
+                if a.dtype.__repr__() != "torch.float64":
+                    raise TypeError("device fields must be float64")
+            self._keep = arrs
+            ptrs = [a.data_ptr() for a in arrs]
+            on_dev = 1
+        else:
+            arrs = [np.ascontiguousarray(np.asarray(a, np.float64)) for a in arrs]
+            sizes = [self.N, self.D * self.N, self.D * self.N, self.N]
+            for a, n in zip(arrs, sizes):
+                if a.size != n:
+                    raise ValueError("field size %d, expected %d" % (a.size, n))
+            self._keep = arrs
+            ptrs = [a.ctypes.data for a in arrs]
+            on_dev = 0
+        self._check(self._lib.lbm_init(self._h, *[ctypes.c_void_p(p) for p in ptrs], on_dev), "lbm_init")
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    @property
+    def t(self):
+        v = ctypes.c_longlong()
+        self._check(self._lib.lbm_time(self._h, ctypes.byref(v)), "lbm_time")
+        return v.value
+
+    @property
+    def launches(self):
+        v = ctypes.c_longlong()
+        self._check(self._lib.lbm_launch_count(self._h, ctypes.byref(v)), "lbm_launch_count")
+        return v.value
+
+    def moments(self, out=None, host_out=None):
+        """dict of alpha_g, u_g (D, N), u_l (D, N), p_k, S_g, S_l.
+
+        With ``out`` a dict of torch float64 CUDA tensors of those shapes, the
+        library writes into them on the device; with ``host_out`` a dict of
+        caller-owned (e.g. pinned) contiguous float64 numpy arrays it writes
+        into those; otherwise it returns new numpy arrays."""
+        N, D = self.N, self.D
+        keys = ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l")
+        if host_out is not None:
+            for k in keys:
+                a = host_out.get(k)
+                if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+                    raise TypeError("host_out[%s] must be contiguous float64" % k)
+            ptrs = [ctypes.c_void_p(host_out[k].ctypes.data) if host_out.get(k) is not None else None for k in keys]
+            self._check(self._lib.lbm_get_moments(self._h, *ptrs, 0), "lbm_get_moments")
+            return host_out
+        if out is not None:
+            keys = ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l")
+            ptrs = [ctypes.c_void_p(out[k].data_ptr()) if k in out else None for k in keys]
+            self._check(self._lib.lbm_get_moments(self._h, *ptrs, 1), "lbm_get_moments")
+            return out
+        res = dict(alpha_g=np.empty(N), u_g=np.empty((D, N)), u_l=np.empty((D, N)), p_k=np.empty(N),
+                   S_g=np.empty(N), S_l=np.empty(N))
+        ptrs = [ctypes.c_void_p(res[k].ctypes.data) for k in ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l")]
+        self._check(self._lib.lbm_get_moments(self._h, *ptrs, 0), "lbm_get_moments")
+        return res
+
+    def populations(self, s):
+        """Full populations of scheme s as numpy (Q, N), library velocity order."""
+        Q = {1: 3, 2: 9, 3: 19}[self.D]
+        out = np.empty((Q, self.N))
+        self._check(self._lib.lbm_get_populations(self._h, int(s), ctypes.c_void_p(out.ctypes.data), 0),
+                    "lbm_get_populations")
+        return out
+
+    def diag(self):
+        out = (ctypes.c_double * 8)()
+        self._check(self._lib.lbm_get_diag(self._h, out), "lbm_get_diag")
+        return np.array(out[:])

@@ -1,0 +1,520 @@
+// Host side of the C ABI declared in include/lbm.h: context lifetime,
+// argument validation, tile selection, the stepping loop (per-step scalars of
+// the lag latch and the inlet ramp of Eq. (transient)) and the FP64
+// diagnostics pipeline.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+cudaError_t launch_step_1(int, const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_step_2(int, const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_step_3(int, const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_moments_1(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_moments_2(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_moments_3(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_pops_1(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_pops_2(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_pops_3(int, const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_init_1(int, const MomArgs &, const double *, const double *, const double *, const double *,
+                          unsigned, cudaStream_t);
+cudaError_t launch_init_2(int, const MomArgs &, const double *, const double *, const double *, const double *,
+                          unsigned, cudaStream_t);
+cudaError_t launch_init_3(int, const MomArgs &, const double *, const double *, const double *, const double *,
+                          unsigned, cudaStream_t);
+
+__global__ void k_diag_final(const double *partials, int nblocks, double *out) {
+  // One warp per diagnostic, each lane sums a fixed strided subset, then a
+  // fixed-order shuffle tree: the result does not depend on scheduling.
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= 8) return;
+  double acc = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    double v = partials[(long long)b * 8 + k];
+    acc = (k == 4) ? fmax(acc, v) : acc + v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double v = __shfl_xor_sync(0xffffffffu, acc, o);
+    acc = (k == 4) ? fmax(acc, v) : acc + v;
+  }
+  if (lane == 0) out[k] = acc;
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+  int lattice, D, Q, prec;
+  int n[3];
+  long long N, plane;
+  lbm_params p;
+  void *pop = nullptr, *held = nullptr;
+  double *partials = nullptr, *diag_dev = nullptr;
+  double *h_diag = nullptr;  // pinned, 8 doubles
+  cudaEvent_t diag_ev = nullptr;
+  int diag_pending = 0;
+  unsigned nblk_flat = 0;
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaStream_t stream = 0;
+  long long t = 0;
+  int initialised = 0, sticky = 0;
+  double r_ag = 0.5, r_al = 0.5;
+  double mass0 = 0.0;
+  int T[3] = {1, 1, 1}, shift[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
+  size_t smem = 0;
+  long long launches = 0;
+  char err[512] = {0};
+};
+
+static int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof c->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CUDA_TRY(c, call)                                                                              \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return set_err((c), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static size_t store_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
+static size_t held_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+
+static cudaError_t dispatch_step(lbm_ctx *c, const StepArgs &a) {
+  dim3 g(c->grid[0], c->grid[1], c->grid[2]), b(c->T[0], c->T[1], c->T[2]);
+  c->launches++;
+  if (c->lattice == 1) return launch_step_1(c->prec, a, g, b, c->smem, c->stream);
+  if (c->lattice == 2) return launch_step_2(c->prec, a, g, b, c->smem, c->stream);
+  return launch_step_3(c->prec, a, g, b, c->smem, c->stream);
+}
+static cudaError_t dispatch_moments(lbm_ctx *c, const MomArgs &ma, int mode) {
+  c->launches++;
+  if (c->lattice == 1) return launch_moments_1(c->prec, ma, mode, c->nblk_flat, c->stream);
+  if (c->lattice == 2) return launch_moments_2(c->prec, ma, mode, c->nblk_flat, c->stream);
+  return launch_moments_3(c->prec, ma, mode, c->nblk_flat, c->stream);
+}
+static cudaError_t dispatch_pops(lbm_ctx *c, const MomArgs &ma, int s) {
+  c->launches++;
+  if (c->lattice == 1) return launch_pops_1(c->prec, ma, s, c->nblk_flat, c->stream);
+  if (c->lattice == 2) return launch_pops_2(c->prec, ma, s, c->nblk_flat, c->stream);
+  return launch_pops_3(c->prec, ma, s, c->nblk_flat, c->stream);
+}
+static cudaError_t dispatch_init(lbm_ctx *c, const MomArgs &ma, const double *a, const double *ug, const double *ul,
+                                 const double *pk) {
+  c->launches++;
+  if (c->lattice == 1) return launch_init_1(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+  if (c->lattice == 2) return launch_init_2(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+  return launch_init_3(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+}
+
+static double ramp(const double mm[2], long long t, int nt) {
+  if (nt <= 0) return mm[1];
+  return (mm[1] - mm[0]) * tanh((double)t / (double)nt) + mm[0];
+}
+
+// Per-step arguments: everything constant plus parity, latch and inlet values.
+static StepArgs make_args(const lbm_ctx *c, long long t) {
+  const lbm_params &p = c->p;
+  StepArgs a;
+  memset(&a, 0, sizeof a);
+  a.pop = c->pop;
+  a.held = c->held;
+  a.plane = c->plane;
+  for (int d = 0; d < 3; d++) {
+    a.n[d] = c->n[d];
+    a.shift[d] = c->shift[d];
+    a.T[d] = c->T[d];
+    a.bc_lo[d] = d < c->D ? p.bc_lo[d] : BC_PERIODIC;
+    a.bc_hi[d] = d < c->D ? p.bc_hi[d] : BC_PERIODIC;
+  }
+  a.parity = (int)(t & 1);
+  a.latch = (t % p.n_gamma) == 0;
+  a.g_axis = p.g_axis;
+  a.tr_axis = -1;
+  for (int d = 0; d < c->D; d++)
+    if (d != p.g_axis) { a.tr_axis = d; break; }
+  a.inlet_lo = p.inlet_lo;
+  a.inlet_hi = p.inlet_hi;
+  a.has_inlet = p.bc_lo[p.g_axis] == BC_INLET;
+  a.has_outlet = p.bc_hi[p.g_axis] == BC_OUTLET;
+  a.R = p.R;
+  a.invR = 1.0 / p.R;
+  a.omega_g = p.omega_g;
+  a.omega_l = p.omega_l;
+  a.omega_a = p.omega_alpha;
+  a.kgrad = p.omega_alpha / CS2;
+  const double w0 = c->lattice == 1 ? 2.0 / 3.0 : (c->lattice == 2 ? 4.0 / 9.0 : 1.0 / 3.0);
+  a.k0 = (1.0 - w0) / w0;
+  if (c->D == 1) {
+    // Eq. (taylor-second31Db): sigma = nu_ef [omega (Pi^eq - Pi) + psi cs2 S]
+    double nug = (1.0 / p.omega_g - 0.5) - CS2 * p.psi_g / p.omega_g;
+    double nul = (1.0 / p.omega_l - 0.5) - CS2 * p.psi_l / p.omega_l;
+    a.A_g = nug * p.omega_g;
+    a.B_g = nug * p.psi_g * CS2;
+    a.A_l = nul * p.omega_l;
+    a.B_l = nul * p.psi_l * CS2;
+  } else {
+    // Eq. (lbm-sigma3): sigma = (1 - omega/2)(Pi^eq - Pi) - cs2 psi/2 S I
+    a.A_g = 1.0 - 0.5 * p.omega_g;
+    a.B_g = -0.5 * CS2 * p.psi_g;
+    a.A_l = 1.0 - 0.5 * p.omega_l;
+    a.B_l = -0.5 * CS2 * p.psi_l;
+  }
+  a.psi_g = p.psi_g;
+  a.psi_l = p.psi_l;
+  a.eta0_g = 1.0 + a.k0 * (1.0 - p.psi_g);
+  a.eta0_l = 1.0 + a.k0 * (1.0 - p.psi_l);
+  a.kappa_I = p.kappa_I;
+  a.kappa_W = p.kappa_W;
+  a.cgw = p.drag_model == LBM_DRAG_CGW;
+  a.buoy = (p.R - 1.0) * p.g_hat;
+  a.gamma = p.gamma;
+  a.afloor = p.alpha_floor;
+  a.spalding = p.spalding_mode;
+  a.r_ag = c->r_ag;
+  a.r_al = c->r_al;
+  a.aIN = ramp(p.in_alpha, t, p.ramp_nt);
+  a.ugIN = ramp(p.in_ug, t, p.ramp_nt);
+  a.ulIN = p.inlet_ul_mode == 1 ? -a.aIN * a.ugIN / (1.0 - a.aIN) : ramp(p.in_ul, t, p.ramp_nt);
+  return a;
+}
+
+static MomArgs make_mom(const lbm_ctx *c, double *out) {
+  MomArgs ma;
+  ma.s = make_args(c, c->t);
+  ma.out = out;
+  ma.N = c->N;
+  ma.partials = c->partials;
+  return ma;
+}
+
+static int ensure_stage(lbm_ctx *c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return LBM_OK;
+  if (c->stage) cudaFree(c->stage);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
+  if (cudaMalloc(&c->stage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, LBM_ENOMEM, "staging allocation of %zu bytes failed", bytes);
+  }
+  c->stage_bytes = bytes;
+  return LBM_OK;
+}
+
+// Tile of the fused kernel: x fastest; the axis of the inlet/outlet faces
+// gets a tile of at least 4 and a shift so that each edge node and its inward
+// neighbour share a block (their values are exchanged in shared memory).
+static int choose_tiles(lbm_ctx *c) {
+  const lbm_params &p = c->p;
+  if (c->D == 1) { c->T[0] = 128; c->T[1] = 1; c->T[2] = 1; }
+  else if (c->D == 2) { c->T[0] = 64; c->T[1] = 4; c->T[2] = 1; }
+  else { c->T[0] = 32; c->T[1] = 4; c->T[2] = 2; }
+  const int ga = p.g_axis;
+  const int io = (p.bc_lo[ga] == LBM_BC_INLET) || (p.bc_hi[ga] == LBM_BC_OUTLET);
+  if (io && c->D == 3 && ga == 2) { c->T[1] = 2; c->T[2] = 4; }
+  for (int d = 0; d < 3; d++) c->shift[d] = 0;
+  if (io) {
+    const int T = c->T[ga], n = c->n[ga];
+    int s = -1;
+    for (int cand = 0; cand <= T - 2; cand++) {
+      if (p.bc_hi[ga] == LBM_BC_OUTLET && ((n - 1 + cand) % T) == 0) continue;
+      s = cand;
+      break;
+    }
+    if (s < 0) return set_err(c, LBM_EINVAL, "no tile shift keeps the outlet pair in one block");
+    c->shift[ga] = s;
+    c->smem = (size_t)c->T[0] * c->T[1] * c->T[2] * XCH * (c->prec == LBM_FP64 ? 8 : 4);
+  } else {
+    c->smem = 0;
+  }
+  for (int d = 0; d < 3; d++) c->grid[d] = (c->n[d] + c->shift[d] + c->T[d] - 1) / c->T[d];
+  return LBM_OK;
+}
+
+extern "C" {
+
+void lbm_default_params(lbm_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->R = 2.0;
+  p->omega_g = p->omega_l = 1.0;
+  p->omega_alpha = 1.5;
+  p->n_gamma = 1;
+  p->spalding_mode = 2;
+  p->alpha_floor = 1e-8;
+  p->precision = LBM_FP32;
+}
+
+int lbm_lattice(int lattice, int *Q, int *v, double *w) {
+  if (lattice < 1 || lattice > 3 || !Q) return LBM_EINVAL;
+  int q_ = lattice == 1 ? 3 : (lattice == 2 ? 9 : 19);
+  *Q = q_;
+  for (int q = 0; q < q_; q++)
+    for (int a = 0; a < 3; a++) {
+      int val = lattice == 1 ? Lattice<1>::v(q, a) : (lattice == 2 ? Lattice<2>::v(q, a) : Lattice<3>::v(q, a));
+      if (v) v[3 * q + a] = val;
+      if (w && a == 0) w[q] = lattice == 1 ? Lattice<1>::w(q) : (lattice == 2 ? Lattice<2>::w(q) : Lattice<3>::w(q));
+    }
+  return LBM_OK;
+}
+
+int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p, lbm_ctx **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!p) return LBM_EINVAL;
+  if (lattice < 1 || lattice > 3 || dim != lattice) return LBM_EINVAL;
+  if (nx < 1 || ny < 1 || nz < 1 || (dim < 2 && ny != 1) || (dim < 3 && nz != 1)) return LBM_EINVAL;
+  if ((long long)nx * ny * nz > (1LL << 34)) return LBM_EINVAL;
+  const lbm_params &q = *p;
+  if (!(q.R >= 1.0) || !(q.omega_g > 0 && q.omega_g < 2) || !(q.omega_l > 0 && q.omega_l < 2) ||
+      !(q.omega_alpha > 0 && q.omega_alpha < 2) || q.n_gamma < 1 || q.spalding_mode < 0 || q.spalding_mode > 2 ||
+      !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 2 ||
+      (q.drag_model != LBM_DRAG_CONST && q.drag_model != LBM_DRAG_CGW) || q.diag_every < 0)
+    return LBM_EINVAL;
+  int dims[3] = {nx, ny, nz};
+  for (int d = 0; d < dim; d++) {
+    for (int side = 0; side < 2; side++) {
+      int bc = side ? q.bc_hi[d] : q.bc_lo[d];
+      if (bc < 0 || bc > 3) return LBM_EINVAL;
+      if (bc == LBM_BC_INLET && !(side == 0 && d == q.g_axis)) return LBM_EINVAL;
+      if (bc == LBM_BC_OUTLET && !(side == 1 && d == q.g_axis)) return LBM_EINVAL;
+    }
+    if ((q.bc_lo[d] == LBM_BC_PERIODIC) != (q.bc_hi[d] == LBM_BC_PERIODIC)) return LBM_EINVAL;
+  }
+  if ((q.bc_lo[q.g_axis] == LBM_BC_INLET || q.bc_hi[q.g_axis] == LBM_BC_OUTLET) && dims[q.g_axis] < 2)
+    return LBM_EINVAL;
+  if (q.bc_lo[q.g_axis] == LBM_BC_INLET && q.inlet_ul_mode == 1 && !(q.in_alpha[0] < 1 && q.in_alpha[1] < 1))
+    return LBM_EINVAL;
+
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ENOMEM;
+  c->lattice = lattice;
+  c->D = dim;
+  c->Q = lattice == 1 ? 3 : (lattice == 2 ? 9 : 19);
+  c->prec = q.precision;
+  c->n[0] = nx; c->n[1] = ny; c->n[2] = nz;
+  c->N = (long long)nx * ny * nz;
+  c->plane = (c->N + 63) / 64 * 64;  // 256-byte aligned planes for every store type
+  c->p = q;
+  c->nblk_flat = (unsigned)((c->N + 255) / 256);
+  int rc = choose_tiles(c);
+  if (rc) { int e = rc; delete c; return e; }
+  size_t pop_bytes = (size_t)6 * c->Q * c->plane * store_size(c->prec);
+  size_t held_bytes = (size_t)3 * c->plane * held_size(c->prec);
+  if (cudaMalloc(&c->pop, pop_bytes) != cudaSuccess || cudaMalloc(&c->held, held_bytes) != cudaSuccess ||
+      cudaMalloc((void **)&c->partials, (size_t)c->nblk_flat * 8 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void **)&c->diag_dev, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void **)&c->h_diag, 8 * sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->diag_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_destroy(c);
+    return LBM_ENOMEM;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx *c, void *s) {
+  if (!c) return LBM_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx *c, const double *alpha_g, const double *u_g, const double *u_l, const double *p_k,
+             int on_device) {
+  if (!c) return LBM_EINVAL;
+  if (!alpha_g || !u_g || !u_l || !p_k) return set_err(c, LBM_EINVAL, "lbm_init: NULL field");
+  const long long N = c->N;
+  const int D = c->D;
+  // deviation reference of the alpha schemes: mean of the initial alpha_g
+  std::vector<double> ha;
+  const double *ah = alpha_g;
+  if (on_device) {
+    ha.resize(N);
+    CUDA_TRY(c, cudaMemcpyAsync(ha.data(), alpha_g, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ah = ha.data();
+  }
+  double sum = 0.0;
+  for (long long i = 0; i < N; i++) {
+    if (!(ah[i] >= 0.0 && ah[i] <= 1.0)) return set_err(c, LBM_EINVAL, "lbm_init: alpha_g[%lld] outside [0,1]", i);
+    sum += ah[i];
+  }
+  c->r_ag = sum / (double)N;
+  c->r_al = 1.0 - c->r_ag;
+  const double *da = alpha_g, *dug = u_g, *dul = u_l, *dpk = p_k;
+  if (!on_device) {
+    int rc = ensure_stage(c, (size_t)(2 + 2 * D) * N * sizeof(double));
+    if (rc) return rc;
+    double *s = (double *)c->stage;
+    CUDA_TRY(c, cudaMemcpyAsync(s, alpha_g, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(s + N, u_g, D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(s + (1 + D) * N, u_l, D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(s + (1 + 2 * D) * N, p_k, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    da = s;
+    dug = s + N;
+    dul = s + (1 + D) * N;
+    dpk = s + (1 + 2 * D) * N;
+  }
+  c->t = 0;
+  MomArgs ma = make_mom(c, nullptr);
+  CUDA_TRY(c, dispatch_init(c, ma, da, dug, dul, dpk));
+  c->mass0 = sum;
+  c->initialised = 1;
+  c->sticky = 0;
+  c->diag_pending = 0;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+// Check the diagnostics a previous lbm_step enqueued, if they have arrived.
+static int check_diag(lbm_ctx *c, int wait) {
+  if (!c->diag_pending) return LBM_OK;
+  if (wait) {
+    CUDA_TRY(c, cudaEventSynchronize(c->diag_ev));
+  } else {
+    cudaError_t q = cudaEventQuery(c->diag_ev);
+    if (q == cudaErrorNotReady) return LBM_OK;
+    if (q != cudaSuccess) return set_err(c, LBM_ECUDA, "diagnostics event: %s", cudaGetErrorString(q));
+  }
+  c->diag_pending = 0;
+  const double *d = c->h_diag;
+  if (d[5] != 0.0 || !isfinite(d[0]) || !isfinite(d[1])) {
+    c->sticky = LBM_ENAN;
+    return set_err(c, LBM_ENAN, "non-finite populations at %.0f nodes", d[5]);
+  }
+  const int closed = c->p.bc_lo[c->p.g_axis] != LBM_BC_INLET && c->p.bc_hi[c->p.g_axis] != LBM_BC_OUTLET;
+  if (closed && c->p.drift_limit > 0 && c->mass0 > 0 && fabs(d[0] - c->mass0) > c->p.drift_limit * c->mass0) {
+    c->sticky = LBM_EDRIFT;
+    return set_err(c, LBM_EDRIFT, "sum(a_g) drifted from %.17g to %.17g", c->mass0, d[0]);
+  }
+  return LBM_OK;
+}
+
+static int enqueue_diag(lbm_ctx *c, double *dev_out) {
+  MomArgs ma = make_mom(c, nullptr);
+  CUDA_TRY(c, dispatch_moments(c, ma, 2));
+  c->launches++;
+  k_diag_final<<<1, 256, 0, c->stream>>>(c->partials, (int)c->nblk_flat, dev_out);
+  CUDA_TRY(c, cudaGetLastError());
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int n) {
+  if (!c || n < 0) return LBM_EINVAL;
+  if (!c->initialised) return set_err(c, LBM_ESTATE, "lbm_step before lbm_init");
+  if (c->sticky) return set_err(c, LBM_ESTATE, "sticky error %d; call lbm_init", c->sticky);
+  int rc = check_diag(c, 0);
+  if (rc) return rc;
+  for (int k = 0; k < n; k++) {
+    StepArgs a = make_args(c, c->t);
+    CUDA_TRY(c, dispatch_step(c, a));
+    c->t++;
+    if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
+      if (c->diag_pending) {
+        rc = check_diag(c, 1);
+        if (rc) return rc;
+      }
+      rc = enqueue_diag(c, c->diag_dev);
+      if (rc) return rc;
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_diag, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaEventRecord(c->diag_ev, c->stream));
+      c->diag_pending = 1;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_get_moments(lbm_ctx *c, double *alpha_g, double *u_g, double *u_l, double *p_k, double *S_g, double *S_l,
+                    int on_device) {
+  if (!c) return LBM_EINVAL;
+  if (!c->initialised) return set_err(c, LBM_ESTATE, "lbm_get_moments before lbm_init");
+  const long long N = c->N;
+  const int D = c->D;
+  int rc = ensure_stage(c, (size_t)(4 + 2 * D) * N * sizeof(double));
+  if (rc) return rc;
+  double *s = (double *)c->stage;
+  MomArgs ma = make_mom(c, s);
+  CUDA_TRY(c, dispatch_moments(c, ma, 1));
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double *dst[6] = {alpha_g, u_g, u_l, p_k, S_g, S_l};
+  long long off[6] = {0, N, (1 + D) * N, (1 + 2 * D) * N, (2 + 2 * D) * N, (3 + 2 * D) * N};
+  long long len[6] = {N, D * N, D * N, N, N, N};
+  for (int k = 0; k < 6; k++)
+    if (dst[k]) CUDA_TRY(c, cudaMemcpyAsync(dst[k], s + off[k], len[k] * sizeof(double), kind, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx *c, int sch, double *out, int on_device) {
+  if (!c || !out || sch < 0 || sch > 5) return LBM_EINVAL;
+  if (!c->initialised) return set_err(c, LBM_ESTATE, "lbm_get_populations before lbm_init");
+  size_t bytes = (size_t)c->Q * c->N * sizeof(double);
+  double *dst = out;
+  if (!on_device) {
+    int rc = ensure_stage(c, bytes);
+    if (rc) return rc;
+    dst = (double *)c->stage;
+  }
+  MomArgs ma = make_mom(c, dst);
+  CUDA_TRY(c, dispatch_pops(c, ma, sch));
+  if (!on_device) CUDA_TRY(c, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_get_diag(lbm_ctx *c, double out[8]) {
+  if (!c || !out) return LBM_EINVAL;
+  if (!c->initialised) return set_err(c, LBM_ESTATE, "lbm_get_diag before lbm_init");
+  int rc = check_diag(c, 1);
+  if (rc && rc != LBM_ENAN && rc != LBM_EDRIFT) return rc;
+  rc = enqueue_diag(c, c->diag_dev);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_time(const lbm_ctx *c, long long *t) {
+  if (!c || !t) return LBM_EINVAL;
+  *t = c->t;
+  return LBM_OK;
+}
+
+int lbm_launch_count(const lbm_ctx *c, long long *n) {
+  if (!c || !n) return LBM_EINVAL;
+  *n = c->launches;
+  return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err : ""; }
+
+int lbm_destroy(lbm_ctx *c) {
+  if (!c) return LBM_OK;
+  if (c->stream || c->pop) cudaStreamSynchronize(c->stream);
+  if (c->pop) cudaFree(c->pop);
+  if (c->held) cudaFree(c->held);
+  if (c->partials) cudaFree(c->partials);
+  if (c->diag_dev) cudaFree(c->diag_dev);
+  if (c->h_diag) cudaFreeHost(c->h_diag);
+  if (c->diag_ev) cudaEventDestroy(c->diag_ev);
+  if (c->stage) cudaFree(c->stage);
+  delete c;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,701 @@
+// Fused collide-and-stream of the six coupled EE-LBM schemes (arXiv
+// 2409.10399, Sec. 2-3) on an AA-pattern, structure-of-arrays store.
+//
+// Store: one buffer of 6*Q planes, plane (s*Q + q) holds direction q of scheme
+// s (0 g, 1 l, 2 alpha_g, 3 alpha_l, 4 beta_g, 5 beta_l) for all N nodes, node
+// index x + nx*(y + ny*z), x fastest.  Every plane keeps deviations
+// f - w_q*r_s (r = 1 for g, l, beta; r = the initial mean alpha for the alpha
+// schemes), and all arithmetic below is written in those deviations, so the
+// pressure coupling (eps_g - 1)/R of Eq. (lbm-phi-l) is formed without the
+// cancellation of 1 + small.
+//
+// AA pattern (one array, in place): on even t node x reads slot (x, q) and
+// writes its post-collision f*(x,q) to slot (x, opp q); on odd t it reads
+// slot (x - v_q, opp q) and writes slot (x + v_q, q).  Each node reads and
+// writes the same set of slots, so no two threads touch the same slot.  A
+// population that would cross a non-periodic face is reflected into the
+// node's own slot (x, opp q) on the write side, carrying the face rule's value
+// (half-way bounce-back, Table 1 inlet, Table 2 outlet), and is read back from
+// slot (x, q) on the odd read side.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
+
+// Per-launch arguments.  Physics constants are precomputed on the host in
+// double; each kernel converts them to its arithmetic type once.
+struct StepArgs {
+  void *pop;            // 6*Q planes of the store type
+  void *held;           // 3 planes: S''_g, S''_l, Lambda' (float, or double for FP64)
+  long long plane;      // elements per plane (>= N, padded)
+  int n[3];             // nx, ny, nz
+  int shift[3];         // tile shift per axis (keeps edge pairs in one block)
+  int T[3];             // tile sizes (blockDim)
+  int parity;           // t & 1
+  int latch;            // t % n_gamma == 0
+  int bc_lo[3], bc_hi[3];
+  int g_axis, tr_axis;  // gravity / inlet-normal axis, first transverse axis (-1 in 1D)
+  int inlet_lo, inlet_hi;
+  int has_inlet, has_outlet;
+  // physics
+  double invR, R, omega_g, omega_l, omega_a, kgrad;  // kgrad = omega_alpha / cs2
+  double A_g, B_g, A_l, B_l;                         // sigma = A (Pi^eq - Pi) + B S'' I
+  double eta0_g, eta0_l, psi_g, psi_l;               // eta_q(psi): rest / moving
+  double k0;                                         // (1 - w_0)/w_0 of Eq. (eta)
+  double kappa_I, kappa_W, buoy, gamma, afloor;
+  int cgw, spalding;
+  double r_ag, r_al;                                 // deviation references of f_alpha
+  double aIN, ugIN, ulIN;                            // inlet values at this t, Eq. (transient)
+};
+
+// ------------------------------------------------------------ store access
+
+template <class S> struct Store;
+template <> struct Store<double> {
+  template <class R> __device__ __forceinline__ static R ld(const double *p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static void st(double *p, R v) { *p = (double)v; }
+};
+template <> struct Store<float> {
+  template <class R> __device__ __forceinline__ static R ld(const float *p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static void st(float *p, R v) { *p = (float)v; }
+};
+template <> struct Store<__half> {
+  template <class R> __device__ __forceinline__ static R ld(const __half *p) {
+    return (R)__half2float(__ldg(p));
+  }
+  template <class R> __device__ __forceinline__ static void st(__half *p, R v) { *p = __float2half_rn((float)v); }
+};
+
+// Node geometry: neighbour coordinates along each axis (with periodic wrap)
+// and whether a step leaves the domain through a non-periodic face.
+struct Geo {
+  int c[3];
+  int p[3], m[3];        // coordinate of +1 / -1 neighbour (wrapped)
+  bool xp[3], xm[3];     // +1 / -1 step crosses a non-periodic face
+  long long node;
+};
+
+__device__ __forceinline__ void make_geo(const StepArgs &a, int D, Geo &g) {
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int n = a.n[d], c = g.c[d];
+    g.p[d] = c + 1;
+    g.m[d] = c - 1;
+    g.xp[d] = false;
+    g.xm[d] = false;
+    if (d < D) {
+      if (g.p[d] >= n) {
+        if (a.bc_hi[d] == BC_PERIODIC) g.p[d] = 0; else g.xp[d] = true;
+      }
+      if (g.m[d] < 0) {
+        if (a.bc_lo[d] == BC_PERIODIC) g.m[d] = n - 1; else g.xm[d] = true;
+      }
+    }
+  }
+  g.node = (long long)g.c[0] + (long long)a.n[0] * ((long long)g.c[1] + (long long)a.n[1] * g.c[2]);
+}
+
+template <class L>
+__device__ __forceinline__ long long shifted_node(const StepArgs &a, const Geo &g, int q, int sign) {
+  // node index of x + sign*v_q with periodic wrap (only valid if not crossing)
+  int cc[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int vv = sign * L::v(q, d);
+    cc[d] = vv > 0 ? g.p[d] : (vv < 0 ? g.m[d] : g.c[d]);
+  }
+  return (long long)cc[0] + (long long)a.n[0] * ((long long)cc[1] + (long long)a.n[1] * cc[2]);
+}
+
+template <class L>
+__device__ __forceinline__ bool crosses(const Geo &g, int q, int sign) {
+  bool x = false;
+#pragma unroll
+  for (int d = 0; d < L::D; d++) {
+    int vv = sign * L::v(q, d);
+    x = x || (vv > 0 && g.xp[d]) || (vv < 0 && g.xm[d]);
+  }
+  return x;
+}
+
+// Face rule for a population leaving the node along q (requires crosses(+1)):
+// a wall on any crossed face wins; the inlet face acts as a wall outside the
+// strip.
+template <class L>
+__device__ __forceinline__ int face_rule(const StepArgs &a, const Geo &g, int q) {
+  int rule = -1;
+#pragma unroll
+  for (int d = 0; d < L::D; d++) {
+    int vv = L::v(q, d);
+    int bc = -1;
+    if (vv > 0 && g.xp[d]) bc = a.bc_hi[d];
+    if (vv < 0 && g.xm[d]) bc = a.bc_lo[d];
+    if (bc == BC_INLET && a.tr_axis >= 0) {
+      const int ct = a.tr_axis == 0 ? g.c[0] : (a.tr_axis == 1 ? g.c[1] : g.c[2]);
+      if (ct < a.inlet_lo || ct >= a.inlet_hi) bc = BC_WALL;
+    }
+    if (bc >= 0 && (rule < 0 || bc == BC_WALL)) rule = bc;
+  }
+  return rule;
+}
+
+// Slot of the read of direction q (AA rule, see the file comment).
+template <class L>
+__device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, int q, int &plane_q) {
+  if (a.parity == 0) {
+    plane_q = q;
+    return g.node;
+  }
+  if (crosses<L>(g, q, -1)) {
+    plane_q = q;
+    return g.node;
+  }
+  plane_q = opp_of(q);
+  return shifted_node<L>(a, g, q, -1);
+}
+
+// Slot of the write of the post-collision population of direction q.
+template <class L>
+__device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g, int q, bool cross, int &plane_q) {
+  if (a.parity == 0 || cross) {
+    plane_q = opp_of(q);
+    return g.node;
+  }
+  plane_q = q;
+  return shifted_node<L>(a, g, q, +1);
+}
+
+// Load all populations of the node (deviations) with the AA read rule.
+template <class L, class S, class R>
+__device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, R f[6][L::Q]) {
+  const S *base = (const S *)a.pop;
+#pragma unroll
+  for (int q = 0; q < L::Q; q++) {
+    int pq;
+    long long idx = read_slot<L>(a, g, q, pq);
+#pragma unroll
+    for (int s = 0; s < 6; s++) f[s][q] = Store<S>::template ld<R>(base + (long long)(s * L::Q + pq) * a.plane + idx);
+  }
+}
+
+// ------------------------------------------------------------- moments
+
+template <class L, class R> struct Moments {
+  R deg, del;            // eps_g - 1, eps_l - 1
+  R ug[3], ul[3];
+  R Pg[6], Pl[6];        // Pi - cs2 I, packed xx, yy, zz, xy, xz, yz
+  R ag, al, Jg[3], Jl[3];
+  R Sg, Sl;              // 1 - beta
+  R alg, all;            // alpha^B
+};
+
+__host__ __device__ constexpr int pidx(int a, int b) {
+  return a == b ? a : ((a + b == 1) ? 3 : ((a + b == 2) ? 4 : 5));
+}
+
+template <class L, class R>
+__device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], Moments<L, R> &m) {
+  constexpr int D = L::D;
+  m.deg = m.del = m.ag = m.al = m.Sg = m.Sl = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) m.ug[d] = m.ul[d] = m.Jg[d] = m.Jl[d] = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; k++) m.Pg[k] = m.Pl[k] = R(0);
+#pragma unroll
+  for (int q = 0; q < L::Q; q++) {
+    m.deg += f[0][q];
+    m.del += f[1][q];
+    m.ag += f[2][q];
+    m.al += f[3][q];
+    m.Sg -= f[4][q];
+    m.Sl -= f[5][q];
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int vd = L::v(q, d);
+      if (vd != 0) {
+        m.ug[d] += vd * f[0][q];
+        m.ul[d] += vd * f[1][q];
+        m.Jg[d] += vd * f[2][q];
+        m.Jl[d] += vd * f[3][q];
+      }
+#pragma unroll
+      for (int e = d; e < D; e++) {
+        const int ve = L::v(q, e);
+        if (vd * ve != 0) {
+          m.Pg[pidx(d, e)] += (vd * ve) * f[0][q];
+          m.Pl[pidx(d, e)] += (vd * ve) * f[1][q];
+        }
+      }
+    }
+  }
+  m.ag += (R)a.r_ag;
+  m.al += (R)a.r_al;
+  if (a.spalding == 0) {
+    m.alg = m.ag;
+    m.all = m.al;
+  } else {
+    // Eq. (spalding) with B(x) = x clamped to [0, 1]
+    R Bg = m.ag < R(0) ? R(0) : (m.ag > R(1) ? R(1) : m.ag);
+    R Bl = m.al < R(0) ? R(0) : (m.al > R(1) ? R(1) : m.al);
+    R sum = Bg + Bl;
+    m.alg = sum > R(0) ? Bg / sum : R(0.5);
+    m.all = R(1) - m.alg;
+  }
+}
+
+// ------------------------------------------------------------ fused step
+
+template <class L, class R>
+__device__ __forceinline__ R vdot(int q, const R u[3]) {
+  R s = R(0);
+#pragma unroll
+  for (int d = 0; d < L::D; d++) {
+    const int vd = L::v(q, d);
+    if (vd == 1) s += u[d];
+    if (vd == -1) s -= u[d];
+  }
+  return s;
+}
+
+// f^eq(alpha, u)_q - w_q*r with the quadratic term of Eq. (equilibrium).
+template <class L, class R>
+__device__ __forceinline__ R feqS_dev(int q, R alpha, const R u[3], R uu, R r) {
+  const R w = (R)L::w(q);
+  const R vu = vdot<L, R>(q, u);
+  return w * (alpha * (R(1) + R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu) - r);
+}
+
+// Values a face rule streams back into the node, as deviations.  xn holds the
+// extrapolation neighbour's values: [0..2] u_g, [3..5] u_l, [6] alpha^B_g,
+// [7] alpha^B_l, [8..10] c_g, [11..13] c_l.
+constexpr int XCH = 14;
+
+template <class L, class S, class R>
+__global__ void __launch_bounds__(256) k_step(const StepArgs a) {
+  constexpr int D = L::D, Q = L::Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *xch = reinterpret_cast<R *>(smem_raw);
+
+  Geo g;
+  g.c[0] = blockIdx.x * a.T[0] + threadIdx.x - a.shift[0];
+  g.c[1] = blockIdx.y * a.T[1] + threadIdx.y - a.shift[1];
+  g.c[2] = blockIdx.z * a.T[2] + threadIdx.z - a.shift[2];
+  const bool active = g.c[0] >= 0 && g.c[0] < a.n[0] && g.c[1] >= 0 && g.c[1] < a.n[1] && g.c[2] >= 0 &&
+                      g.c[2] < a.n[2];
+  const int tid = threadIdx.x + a.T[0] * (threadIdx.y + a.T[1] * threadIdx.z);
+  const int gax = a.g_axis;
+  const int gstride = gax == 0 ? 1 : (gax == 1 ? a.T[0] : a.T[0] * a.T[1]);
+  // does this block hold an inlet/outlet edge row (block-uniform)?
+  const int Tg = gax == 0 ? a.T[0] : (gax == 1 ? a.T[1] : a.T[2]);
+  const int ng = gax == 0 ? a.n[0] : (gax == 1 ? a.n[1] : a.n[2]);
+  const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
+  const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
+  const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
+
+  R f[6][Q];
+  Moments<L, R> m;
+  R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
+  if (active) {
+    make_geo(a, D, g);
+    load_node<L, S, R>(a, g, f);
+    moments<L, R>(a, f, m);
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      cg[d] = m.all * (m.ug[d] - m.ul[d]);  // Eq. (velocitybeta) with beta = 1
+      cl[d] = m.alg * (m.ul[d] - m.ug[d]);
+    }
+  }
+  if (blk_xch) {
+    if (active) {
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        xch[tid * XCH + d] = m.ug[d] * (d < D);
+        xch[tid * XCH + 3 + d] = m.ul[d] * (d < D);
+        xch[tid * XCH + 8 + d] = cg[d];
+        xch[tid * XCH + 11 + d] = cl[d];
+      }
+      xch[tid * XCH + 6] = m.alg;
+      xch[tid * XCH + 7] = m.all;
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+
+  const R R_ = (R)a.R, invR = (R)a.invR;
+  // ---- sources: Eq. (lbmbetataylorzeroth5), dashpot Eqs. (lbm-cont-g1Dhat),
+  //      (lbm-cont-l1Dhat) third strategy with phi*eps_l - 1 = (eps_g - 1)/R
+  const R dPl = m.deg * invR;
+  R ug2 = R(0), ul2 = R(0);
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    ug2 += m.ug[d] * m.ug[d];
+    ul2 += m.ul[d] * m.ul[d];
+  }
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  H *held = (H *)a.held;
+  R Spp_g, Spp_l, Lam;
+  if (a.latch) {
+    Spp_g = m.Sg - (R)a.gamma * ug2 * m.deg;
+    Spp_l = m.Sl - (R)a.gamma * ul2 * dPl;
+    Lam = m.alg * m.all * (m.alg + m.all * R_);  // Eq. (Lambda)
+    held[g.node] = (H)Spp_g;
+    held[a.plane + g.node] = (H)Spp_l;
+    held[2 * a.plane + g.node] = (H)Lam;
+    Spp_g = (R)(H)Spp_g;
+    Spp_l = (R)(H)Spp_l;
+    Lam = (R)(H)Lam;
+  } else {
+    Spp_g = (R)held[g.node];
+    Spp_l = (R)held[a.plane + g.node];
+    Lam = (R)held[2 * a.plane + g.node];
+  }
+
+  // ---- grad(alpha): Eq. (gradlnalpha) times alpha, corrected by Eq. (spalding2);
+  //      grad^G alpha_l = -grad^G alpha_g
+  R gG[3] = {R(0), R(0), R(0)};
+  const R kg = (R)a.kgrad;
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    R grg = kg * (m.ag * m.ug[d] - m.Jg[d]);
+    R grl = kg * (m.al * m.ul[d] - m.Jl[d]);
+    gG[d] = R(0.5) * (grg - grl);
+  }
+
+  // ---- stress sigma = A (Pi^eq - Pi) + B S'' I (Eq. (lbm-sigma3); D = 1:
+  //      Eq. (taylor-second31Db)), Pi^eq from Eq. (secondtensoreq)
+  R sgG[3], slG[3];
+  {
+    const R cs2 = R(1.0 / 3.0);
+    R Ng[6], Nl[6];
+#pragma unroll
+    for (int d = 0; d < D; d++)
+#pragma unroll
+      for (int e = d; e < D; e++) {
+        const int k = pidx(d, e);
+        Ng[k] = m.ug[d] * m.ug[e] - m.Pg[k] + (d == e ? cs2 * m.deg : R(0));
+        Nl[k] = m.ul[d] * m.ul[e] - m.Pl[k] + (d == e ? cs2 * dPl : R(0));
+      }
+    const R Ag = (R)a.A_g, Al = (R)a.A_l, Bg = (R)a.B_g * Spp_g, Bl = (R)a.B_l * Spp_l;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      R sg = Bg * gG[d], sl = -Bl * gG[d];
+#pragma unroll
+      for (int e = 0; e < D; e++) {
+        const int k = pidx(d, e);
+        sg += Ag * Ng[k] * gG[e];
+        sl -= Al * Nl[k] * gG[e];
+      }
+      sgG[d] = sg;
+      slG[d] = sl;
+    }
+  }
+
+  // ---- drag (Eq. (interphasemomentum), CGW Eq. (CliftGraceWeber)), wall
+  //      friction (Eq. (wallmomentum1D)), forces Eqs. (Gg), (Gl), (Gg1D)
+  R Gg[3] = {R(0), R(0), R(0)}, Gl[3] = {R(0), R(0), R(0)};
+  {
+    const R KI = a.cgw ? (R)a.kappa_I * Lam : (R)a.kappa_I;
+    const R KW = a.cgw ? (R)a.kappa_W * Lam : (R)a.kappa_W;
+    R du[3], du2 = R(0);
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      du[d] = m.ul[d] - m.ug[d];
+      du2 += du[d] * du[d];
+    }
+    const R ndu = sqrt(du2), nul = sqrt(ul2);
+    const R fl = (R)a.afloor;
+    const R inv_g = R(1) / (m.alg > fl ? m.alg : fl);
+    const R inv_l = R(1) / (m.all > fl ? m.all : fl);
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      Gg[d] = Spp_g * m.ug[d] + (sgG[d] + KI * ndu * du[d]) * inv_g + (d == a.g_axis ? (R)a.buoy : R(0));
+      Gl[d] = Spp_l * m.ul[d] + slG[d] * inv_l - (KI * ndu * du[d] + KW * nul * m.ul[d]) * inv_l * invR;
+    }
+  }
+
+  // ---- collisions and AA store with face rules
+  S *base = (S *)a.pop;
+  const R om_g = (R)a.omega_g, om_l = (R)a.omega_l, om_a = (R)a.omega_a;
+  const R k0 = (R)a.k0;
+  const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
+  const R rag = (R)a.r_ag, ral = (R)a.r_al;
+  R c2g = R(0), c2l = R(0);
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    c2g += cg[d] * cg[d];
+    c2l += cl[d] * cl[d];
+  }
+  // equilibrium offsets of f_I^eq - w: rest and moving directions, Eq. (eta)
+  const R eI_g0 = m.deg, eI_gq = m.deg;                 // phi_g = 1
+  const R eI_l0 = m.del + k0 * (m.del - dPl), eI_lq = dPl;
+  const R eL_g0 = Spp_g * (R)a.eta0_g, eL_gq = Spp_g * (R)a.psi_g;
+  const R eL_l0 = Spp_l * (R)a.eta0_l, eL_lq = Spp_l * (R)a.psi_l;
+
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const R w = (R)L::w(q);
+    const R vug = vdot<L, R>(q, m.ug), vul = vdot<L, R>(q, m.ul);
+    const R vGg = vdot<L, R>(q, Gg), vGl = vdot<L, R>(q, Gl);
+    R out[6];
+    out[0] = f[0][q] + om_g * (w * ((q == 0 ? eI_g0 : eI_gq) + R(3) * vug + R(4.5) * vug * vug - R(1.5) * ug2) - f[0][q]) +
+             w * ((q == 0 ? eL_g0 : eL_gq) + R(3) * vGg);
+    out[1] = f[1][q] + om_l * (w * ((q == 0 ? eI_l0 : eI_lq) + R(3) * vul + R(4.5) * vul * vul - R(1.5) * ul2) - f[1][q]) +
+             w * ((q == 0 ? eL_l0 : eL_lq) + R(3) * vGl);
+    out[2] = f[2][q] + om_a * (feqS_dev<L, R>(q, aeq_g, m.ug, ug2, rag) - f[2][q]);
+    out[3] = f[3][q] + om_a * (feqS_dev<L, R>(q, aeq_l, m.ul, ul2, ral) - f[3][q]);
+    out[4] = feqS_dev<L, R>(q, R(1), cg, c2g, R(1));
+    out[5] = feqS_dev<L, R>(q, R(1), cl, c2l, R(1));
+
+    const bool cross = crosses<L>(g, q, +1);
+    if (cross) {
+      const int rule = face_rule<L>(a, g, q);
+      const int qo = opp_of(q);
+      if (rule == BC_INLET) {
+        // Table 1: f_g, f_l BB(I) (Eq. (BB): -2 w v.u^B/cs2), f_alpha EQ(S)
+        // Dirichlet, f_beta EQ(S) with beta and c extrapolated full-way.
+        const R vq = (R)(gax == 0 ? L::v(q, 0) : (gax == 1 ? L::v(q, 1) : L::v(q, 2)));
+        out[0] -= R(6) * w * vq * (R)a.ugIN;
+        out[1] -= R(6) * w * vq * (R)a.ulIN;
+        R uin[3], lin[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          uin[d] = d == gax ? (R)a.ugIN : R(0);
+          lin[d] = d == gax ? (R)a.ulIN : R(0);
+        }
+        out[2] = feqS_dev<L, R>(qo, (R)a.aIN, uin, (R)a.ugIN * (R)a.ugIN, rag);
+        out[3] = feqS_dev<L, R>(qo, R(1) - (R)a.aIN, lin, (R)a.ulIN * (R)a.ulIN, ral);
+        const R *xn = xch + (tid + gstride) * XCH;
+        R cb[3] = {R(0), R(0), R(0)}, cc[3] = {R(0), R(0), R(0)}, cb2 = R(0), cc2 = R(0);
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+          cb[d] = R(2) * cg[d] - xn[8 + d];
+          cc[d] = R(2) * cl[d] - xn[11 + d];
+          cb2 += cb[d] * cb[d];
+          cc2 += cc[d] * cc[d];
+        }
+        out[4] = feqS_dev<L, R>(qo, R(1), cb, cb2, R(1));
+        out[5] = feqS_dev<L, R>(qo, R(1), cc, cc2, R(1));
+      } else if (rule == BC_OUTLET) {
+        // Table 2: f_g, f_l ABB(I) with eps = 1 (so phi = 1) and u EX(hw);
+        // f_alpha ABB(S) with alpha, u EX(hw); f_beta EQ(S) with c EX(fw).
+        const R *xn = xch + (tid - gstride) * XCH;
+        R ubg[3] = {R(0), R(0), R(0)}, ubl[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)},
+          cc[3] = {R(0), R(0), R(0)};
+        R ubg2 = R(0), ubl2 = R(0), cb2 = R(0), cc2 = R(0);
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+          ubg[d] = R(1.5) * m.ug[d] - R(0.5) * xn[d];
+          ubl[d] = R(1.5) * m.ul[d] - R(0.5) * xn[3 + d];
+          cb[d] = R(2) * cg[d] - xn[8 + d];
+          cc[d] = R(2) * cl[d] - xn[11 + d];
+          ubg2 += ubg[d] * ubg[d];
+          ubl2 += ubl[d] * ubl[d];
+          cb2 += cb[d] * cb[d];
+          cc2 += cc[d] * cc[d];
+        }
+        const R vbg = vdot<L, R>(q, ubg), vbl = vdot<L, R>(q, ubl);
+        const R qg = R(4.5) * vbg * vbg - R(1.5) * ubg2, ql = R(4.5) * vbl * vbl - R(1.5) * ubl2;
+        out[0] = -out[0] + R(2) * w * qg;
+        out[1] = -out[1] + R(2) * w * ql;
+        const R abg = R(1.5) * m.alg - R(0.5) * xn[6];
+        const R abl = R(1.5) * m.all - R(0.5) * xn[7];
+        out[2] = -out[2] - R(2) * w * rag + R(2) * w * abg * (R(1) + qg);
+        out[3] = -out[3] - R(2) * w * ral + R(2) * w * abl * (R(1) + ql);
+        out[4] = feqS_dev<L, R>(qo, R(1), cb, cb2, R(1));
+        out[5] = feqS_dev<L, R>(qo, R(1), cc, cc2, R(1));
+      }
+      // BC_WALL: half-way bounce-back keeps out[] as is
+    }
+    int pq;
+    const long long idx = write_slot<L>(a, g, q, cross, pq);
+#pragma unroll
+    for (int s = 0; s < 6; s++) Store<S>::template st<R>(base + (long long)(s * Q + pq) * a.plane + idx, out[s]);
+  }
+}
+
+// --------------------------------------------------- moments / diagnostics
+
+// mode bit 1: write fields (FP64): alpha_g^B, u_g (D planes), u_l (D planes),
+// p_k, S_g, S_l at out + k*N; mode bit 2: per-block diagnostic partials.
+struct MomArgs {
+  StepArgs s;
+  double *out;
+  long long N;
+  double *partials;  // gridDim.x * 8
+};
+
+template <class R>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One thread per node over a flat 1D grid (block 256); FP64 block reduction
+// of the eight diagnostics: warp shuffles, then one value per warp in shared
+// memory, then warp 0.
+template <class L, class S, class R>
+__global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
+  constexpr int D = L::D, Q = L::Q;
+  const StepArgs &a = ma.s;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < ma.N) {
+    Geo g;
+    g.c[0] = (int)(i % a.n[0]);
+    g.c[1] = (int)((i / a.n[0]) % a.n[1]);
+    g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
+    make_geo(a, D, g);
+    R f[6][Q];
+    load_node<L, S, R>(a, g, f);
+    Moments<L, R> m;
+    moments<L, R>(a, f, m);
+    if (mode & 1) {
+      double *o = ma.out;
+      const long long N = ma.N;
+      o[i] = (double)m.alg;
+      for (int d = 0; d < D; d++) {
+        o[(1 + d) * N + i] = (double)m.ug[d];
+        o[(1 + D + d) * N + i] = (double)m.ul[d];
+      }
+      o[(1 + 2 * D) * N + i] = (1.0 / 3.0) * (1.0 + (double)m.deg);
+      o[(2 + 2 * D) * N + i] = (double)m.Sg;
+      o[(3 + 2 * D) * N + i] = (double)m.Sl;
+    }
+    if (mode & 2) {
+      bool bad = false;
+#pragma unroll
+      for (int s = 0; s < 6; s++)
+#pragma unroll
+        for (int q = 0; q < Q; q++) bad = bad || !isfinite((double)f[s][q]);
+      double ug2 = 0, ul2 = 0;
+      for (int d = 0; d < D; d++) {
+        ug2 += (double)m.ug[d] * (double)m.ug[d];
+        ul2 += (double)m.ul[d] * (double)m.ul[d];
+      }
+      double sum = (double)m.ag + (double)m.al - 1.0;
+      v[0] = m.ag;
+      v[1] = m.al;
+      v[2] = m.alg;
+      v[3] = sum * sum;
+      v[4] = sqrt(fmax(ug2, ul2));
+      v[5] = bad ? 1.0 : 0.0;
+      v[6] = m.deg;
+      v[7] = m.del;
+    }
+  }
+  if (mode & 2) {
+    __shared__ double red[8][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = (k == 4) ? warp_max(v[k]) : warp_sum<R>(v[k]);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 8; k++) red[k][wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        double x = lane < nw ? red[k][lane] : (k == 4 ? 0.0 : 0.0);
+        x = (k == 4) ? warp_max(x) : warp_sum<R>(x);
+        if (lane == 0) ma.partials[(long long)blockIdx.x * 8 + k] = x;
+      }
+    }
+  }
+}
+
+// Final pass of the diagnostics: one block sums the per-block partials in a
+// fixed order (deterministic) into out[8].
+__global__ void k_diag_final(const double *partials, int nblocks, double *out);
+
+// Full populations (f, not deviations) of scheme s in [q][node] order.
+template <class L, class S, class R>
+__global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
+  constexpr int D = L::D, Q = L::Q;
+  const StepArgs &a = ma.s;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ma.N) return;
+  Geo g;
+  g.c[0] = (int)(i % a.n[0]);
+  g.c[1] = (int)((i / a.n[0]) % a.n[1]);
+  g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
+  make_geo(a, D, g);
+  const S *base = (const S *)a.pop;
+  const double r = s == 2 ? a.r_ag : (s == 3 ? a.r_al : 1.0);
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    int pq;
+    long long idx = read_slot<L>(a, g, q, pq);
+    double dv = Store<S>::template ld<double>(base + (long long)(s * Q + pq) * a.plane + idx);
+    ma.out[(long long)q * ma.N + i] = dv + L::w(q) * r;
+  }
+}
+
+// ----------------------------------------------------------------- init
+
+// Equilibria of every scheme from FP64 fields (Sec. 2, initial state), written
+// in the even-step layout (slot (x, q) holds f(x, q)); held S'' = 0, Lambda' =
+// Lambda(alpha_g).  Computed in double, stored in S.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *alpha_g, const double *u_g,
+                                             const double *u_l, const double *p_k) {
+  constexpr int D = L::D, Q = L::Q;
+  const StepArgs &a = ma.s;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = ma.N;
+  if (i >= N) return;
+  double ug[3] = {0, 0, 0}, ul[3] = {0, 0, 0}, cg[3] = {0, 0, 0}, cl[3] = {0, 0, 0};
+  for (int d = 0; d < D; d++) {
+    ug[d] = u_g[d * N + i];
+    ul[d] = u_l[d * N + i];
+  }
+  const double ag = alpha_g[i], al = 1.0 - ag;
+  const double deg = p_k[i] * 3.0 - 1.0;  // eps_g - 1, Eq. (sigmag1D); eps_l = 1
+  const double dPl = deg * a.invR;        // phi*eps_l - 1, Eq. (lbm-phi-l)
+  double ug2 = 0, ul2 = 0, cg2 = 0, cl2 = 0;
+  for (int d = 0; d < D; d++) {
+    cg[d] = al * (ug[d] - ul[d]);
+    cl[d] = ag * (ul[d] - ug[d]);
+    ug2 += ug[d] * ug[d];
+    ul2 += ul[d] * ul[d];
+    cg2 += cg[d] * cg[d];
+    cl2 += cl[d] * cl[d];
+  }
+  S *base = (S *)a.pop;
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const double w = L::w(q);
+    const double vug = vdot<L, double>(q, ug), vul = vdot<L, double>(q, ul);
+    double o[6];
+    o[0] = w * (deg + 3.0 * vug + 4.5 * vug * vug - 1.5 * ug2);
+    o[1] = w * ((q == 0 ? a.k0 * (0.0 - dPl) : dPl) + 3.0 * vul + 4.5 * vul * vul - 1.5 * ul2);
+    o[2] = feqS_dev<L, double>(q, ag, ug, ug2, a.r_ag);
+    o[3] = feqS_dev<L, double>(q, al, ul, ul2, a.r_al);
+    o[4] = feqS_dev<L, double>(q, 1.0, cg, cg2, 1.0);
+    o[5] = feqS_dev<L, double>(q, 1.0, cl, cl2, 1.0);
+#pragma unroll
+    for (int s = 0; s < 6; s++) Store<S>::template st<double>(base + (long long)(s * Q + q) * a.plane + i, o[s]);
+  }
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  H *held = (H *)a.held;
+  held[i] = (H)0;
+  held[a.plane + i] = (H)0;
+  held[2 * a.plane + i] = (H)(ag * al * (ag + al * a.R));
+}
+
+}  // namespace lbm

@@ -1,0 +1,64 @@
+// Launchers of one lattice for the three storage/arithmetic precisions.
+// Included by exactly one translation unit per lattice (lbm_d1q3.cu, ...).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <int LAT>
+struct Launch {
+  using L = Lattice<LAT>;
+  static cudaError_t step(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    if (prec == 0) k_step<L, double, double><<<grid, block, smem, st>>>(a);
+    else if (prec == 1) k_step<L, float, float><<<grid, block, smem, st>>>(a);
+    else k_step<L, __half, float><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t moments(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
+    if (prec == 0) k_moments<L, double, double><<<nblk, 256, 0, st>>>(ma, mode);
+    else if (prec == 1) k_moments<L, float, float><<<nblk, 256, 0, st>>>(ma, mode);
+    else k_moments<L, __half, float><<<nblk, 256, 0, st>>>(ma, mode);
+    return cudaGetLastError();
+  }
+  static cudaError_t pops(int prec, const MomArgs &ma, int s, unsigned nblk, cudaStream_t st) {
+    if (prec == 0) k_pops<L, double, double><<<nblk, 256, 0, st>>>(ma, s);
+    else if (prec == 1) k_pops<L, float, float><<<nblk, 256, 0, st>>>(ma, s);
+    else k_pops<L, __half, float><<<nblk, 256, 0, st>>>(ma, s);
+    return cudaGetLastError();
+  }
+  static cudaError_t init(int prec, const MomArgs &ma, const double *a, const double *ug, const double *ul,
+                          const double *pk, unsigned nblk, cudaStream_t st) {
+    if (prec == 0) k_init<L, double><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    else if (prec == 1) k_init<L, float><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    else k_init<L, __half><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    return cudaGetLastError();
+  }
+};
+
+// Entry points exported by the per-lattice translation units.
+cudaError_t launch_step(int lat, int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+cudaError_t launch_moments(int lat, int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st);
+cudaError_t launch_pops(int lat, int prec, const MomArgs &ma, int s, unsigned nblk, cudaStream_t st);
+cudaError_t launch_init(int lat, int prec, const MomArgs &ma, const double *a, const double *ug, const double *ul,
+                        const double *pk, unsigned nblk, cudaStream_t st);
+
+}  // namespace lbm
+
+#define LBM_DEFINE_LATTICE_LAUNCHERS(LAT)                                                                      \
+  namespace lbm {                                                                                            \
+  cudaError_t launch_step_##LAT(int prec, const StepArgs &a, dim3 g, dim3 b, size_t sm, cudaStream_t st) {    \
+    return Launch<LAT>::step(prec, a, g, b, sm, st);                                                         \
+  }                                                                                                          \
+  cudaError_t launch_moments_##LAT(int prec, const MomArgs &ma, int mode, unsigned n, cudaStream_t st) {      \
+    return Launch<LAT>::moments(prec, ma, mode, n, st);                                                      \
+  }                                                                                                          \
+  cudaError_t launch_pops_##LAT(int prec, const MomArgs &ma, int s, unsigned n, cudaStream_t st) {            \
+    return Launch<LAT>::pops(prec, ma, s, n, st);                                                            \
+  }                                                                                                          \
+  cudaError_t launch_init_##LAT(int prec, const MomArgs &ma, const double *a, const double *ug,               \
+                                const double *ul, const double *pk, unsigned n, cudaStream_t st) {            \
+    return Launch<LAT>::init(prec, ma, a, ug, ul, pk, n, st);                                                \
+  }                                                                                                          \
+  }

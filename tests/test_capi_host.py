@@ -1,0 +1,72 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function include/lbm.h declares, and its host-only entry points (defaults,
+velocity sets) agree with the oracle's independent lattice construction.
+No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+import paper_2409_10399_gb300 as lbm
+from oracle import params as oparams
+from paper_2409_10399_gb300 import params as lparams
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load_library()
+    names = header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_params_struct_layout_matches_header_defaults():
+    p = lbm.default_params()
+    assert p.R == 2.0 and p.omega_g == 1.0 and p.omega_alpha == 1.5 and p.n_gamma == 1
+    assert p.spalding_mode == 2 and p.alpha_floor == 1e-8 and p.precision == 1
+    assert list(p.bc_lo) == [0, 0, 0] and p.diag_every == 0
+
+
+@pytest.mark.parametrize("lat", ["D1Q3", "D2Q9", "D3Q19"])
+def test_lattice_tables_match_oracle(lat):
+    v, w = lbm.lattice_tables(lat)
+    o = oracle.Oracle(lat, (2, 2 if lat != "D1Q3" else 1, 2 if lat == "D3Q19" else 1), {})
+    vo, wo, _ = o.lattice_tables()
+    mine = {tuple(r): x for r, x in zip(v.tolist(), w)}
+    ref = {tuple(r): x for r, x in zip(vo.tolist(), wo)}
+    assert mine == ref
+    assert np.all(v[0] == 0)
+    # opposite directions adjacent: opp(q) = q+1 for odd q
+    for q in range(1, len(w), 2):
+        assert np.all(v[q] == -v[q + 1])
+
+
+def test_invalid_lattice_rejected_without_gpu():
+    lib = lbm.load_library()
+    Q = ctypes.c_int()
+    assert lib.lbm_lattice(4, ctypes.byref(Q), None, None) == -1
+
+
+@pytest.mark.parametrize("name", ["column1d", "box2d", "column3d"])
+def test_parameter_helpers_agree(name):
+    ph = lbm_inputs.WORKLOADS[name]["physics"]
+    a = oparams.lattice_params(ph)
+    b = lparams.lattice_params(ph)
+    for k, v in a.items():
+        assert k in b
+        if isinstance(v, float):
+            assert b[k] == pytest.approx(v, rel=1e-14, abs=0), k
+        else:
+            assert tuple(np.atleast_1d(b[k])) == tuple(np.atleast_1d(v)), k

@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Bars (relative L2 over a whole field, on alpha_g, u_g, u_l, p_k): 1e-12 for
+FP64, 1e-5 for FP32, 1e-3 for FP16-stored deviations.  Sizes span several
+tiles with ragged tails; cases cover all three lattices, walls, periodic axes,
+the inlet strip (Table 1), the outlet (Table 2), both drag models, the lag
+latch and the Spalding modes, plus edge cases (zero steps, odd step counts,
+one-node-wide periodic axes).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+import paper_2409_10399_gb300 as lbm
+from oracle import params as oparams
+from paper_2409_10399_gb300 import params as lparams
+
+pytestmark = pytest.mark.gpu
+
+PER, WALL, INLET, OUTLET = 0, 1, 2, 3
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16dev": 1e-3}
+S_ATOL = {"fp64": 1e-14, "fp32": 1e-8, "fp16dev": 1e-5}
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def run_pair(lat, dims, p, fields, steps, prec, threads=8):
+    D = lbm.LATTICE[lat]
+    dims3 = tuple(dims) + (1,) * (3 - len(dims))
+    o = oracle.Oracle(lat, dims3, p, threads=threads)
+    o.init(**fields)
+    o.step(steps)
+    ref = o.moments()
+    pg = dict(p)
+    pg["precision"] = prec
+    s = lbm.Simulation(lat, dims3, pg)
+    s.init(**fields)
+    s.step(steps)
+    got = s.moments()
+    return got, ref, s, o
+
+
+def assert_parity(got, ref, prec, ctx=""):
+    tol = TOL[prec]
+    for k in ("alpha_g", "u_g", "u_l", "p_k"):
+        e = rel(got[k], ref[k])
+        assert e <= tol, "%s %s rel L2 %.3e > %.1e" % (ctx, k, e, tol)
+    for k in ("S_g", "S_l"):
+        e = np.abs(got[k] - ref[k]).max()
+        assert e <= S_ATOL[prec], "%s %s max abs %.3e" % (ctx, k, e)
+
+
+BASE = dict(R=1000.0, omega_g=0.6, omega_l=120.0 / 67.0, omega_alpha=1.5, drag_model=1, kappa_I=2.4e-4,
+            kappa_W=0.0, g_hat=1e-6 / 999.0, gamma=1.0, n_gamma=7, spalding_mode=2, alpha_floor=1e-8)
+
+CASES = {
+    # 2D box, periodic x, walls y (ragged in both axes vs the 64x4 tile)
+    "d2q9_walls": ("D2Q9", (70, 37), dict(BASE, g_axis=1, bc_lo=(PER, WALL, 0), bc_hi=(PER, WALL, 0)), 300),
+    # 2D box with the bottom inlet strip of Table 1 and zero net volume flux
+    "d2q9_strip": ("D2Q9", (72, 45), dict(BASE, g_axis=1, bc_lo=(PER, INLET, 0), bc_hi=(PER, WALL, 0),
+                                          inlet_lo=20, inlet_hi=52, in_alpha=(0.01, 0.3), in_ug=(4.3e-4, 4.3e-3),
+                                          ramp_nt=60, inlet_ul_mode=1), 250),
+    # 2D with an outlet (Table 2) on the top face, walls on x, CONST drag, Spalding 1
+    "d2q9_outlet": ("D2Q9", (33, 30), dict(BASE, R=20.0, drag_model=0, kappa_I=1e-2, kappa_W=2e-3, g_axis=1,
+                                           g_hat=1e-5, spalding_mode=1, n_gamma=1,
+                                           bc_lo=(WALL, WALL, 0), bc_hi=(WALL, OUTLET, 0)), 200),
+    # 2D, gravity along x, inlet on x low face, strip in y, walls in y
+    "d2q9_xinlet": ("D2Q9", (41, 22), dict(BASE, R=50.0, g_axis=0, g_hat=2e-6, bc_lo=(INLET, WALL, 0),
+                                           bc_hi=(OUTLET, WALL, 0), inlet_lo=5, inlet_hi=17, in_alpha=(0.05, 0.4),
+                                           in_ug=(1e-3, 4e-3), in_ul=(0.0, 5e-4), ramp_nt=30), 150),
+    # 3D, walls on four sides, periodic z
+    "d3q19_walls": ("D3Q19", (20, 18, 13), dict(BASE, g_axis=2, bc_lo=(WALL, WALL, PER), bc_hi=(WALL, WALL, PER)),
+                    80),
+    # 3D with an inlet strip on the bottom z face (tile shift along z)
+    "d3q19_strip": ("D3Q19", (12, 10, 11), dict(BASE, g_axis=2, bc_lo=(PER, WALL, INLET), bc_hi=(PER, WALL, WALL),
+                                                inlet_lo=3, inlet_hi=9, in_alpha=(0.02, 0.3), in_ug=(1e-3, 4e-3),
+                                                ramp_nt=20, inlet_ul_mode=1), 60),
+    # 1D column with wall friction, psi != 0 (1D stress form)
+    "d1q3_walls": ("D1Q3", (300,), dict(BASE, kappa_W=2.4e-4, psi_g=0.2, psi_l=0.1, g_axis=0,
+                                        bc_lo=(WALL, 0, 0), bc_hi=(WALL, 0, 0)), 500),
+    # 1D open tube of Sec. 3.6 (Table 1 inlet, Table 2 outlet), ragged vs the 128 tile
+    "d1q3_tube": ("D1Q3", (201,), dict(R=2.0, omega_g=0.6, omega_l=0.6, omega_alpha=1.9, drag_model=0,
+                                       kappa_I=1e-2, kappa_W=1e-2, g_hat=1e-6, g_axis=0, n_gamma=1,
+                                       bc_lo=(INLET, 0, 0), bc_hi=(OUTLET, 0, 0), in_alpha=(0.01, 0.8),
+                                       in_ug=(1e-3, 1e-2), in_ul=(0.0, 1e-3), ramp_nt=200), 700),
+}
+
+
+def case_fields(lat, dims, seed):
+    D = lbm.LATTICE[lat]
+    return lbm_inputs.fields_random(D, dims, seed=seed, alpha=(0.05, 0.6), u_amp=2e-3, pk_amp=1e-5)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parity_cases(name, prec):
+    lat, dims, p, steps = CASES[name]
+    f = case_fields(lat, dims, seed=zlib.crc32(name.encode()) % 997)
+    got, ref, _, _ = run_pair(lat, dims, p, f, steps, prec)
+    assert_parity(got, ref, prec, name)
+
+
+@pytest.mark.parametrize("name", ["d2q9_walls", "d3q19_walls", "d2q9_strip"])
+def test_parity_fp16dev(name):
+    lat, dims, p, steps = CASES[name]
+    f = case_fields(lat, dims, seed=5)
+    got, ref, _, _ = run_pair(lat, dims, p, f, min(steps, 100), "fp16dev")
+    assert_parity(got, ref, "fp16dev", name)
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 3])
+def test_populations_and_parity_of_steps(steps):
+    """Every population of every scheme after 0..3 steps (both AA parities)."""
+    lat, dims, p, _ = CASES["d2q9_strip"]
+    f = case_fields(lat, dims, seed=3)
+    got, ref, s, o = run_pair(lat, dims, p, f, steps, "fp64")
+    v, _ = lbm.lattice_tables(lat)
+    vo, _, _ = o.lattice_tables()
+    perm = [int(np.where((vo == r).all(1))[0][0]) for r in v]
+    for sch in range(6):
+        a = s.populations(sch)
+        b = o.pops(sch)[perm]
+        assert np.abs(a - b).max() <= 1e-15 * max(1.0, np.abs(b).max()), sch
+    assert s.t == steps
+
+
+def test_diagnostics_match_oracle():
+    lat, dims, p, steps = CASES["d3q19_walls"]
+    f = case_fields(lat, dims, seed=9)
+    got, ref, s, o = run_pair(lat, dims, p, f, 31, "fp64")
+    a, b = s.diag(), o.diag()
+    for k in (0, 1, 2, 4):
+        assert a[k] == pytest.approx(b[k], rel=1e-12)
+    assert a[3] == pytest.approx(b[3], rel=1e-6, abs=1e-20)
+    assert a[5] == b[5] == 0
+    assert a[6] == pytest.approx(b[6], rel=1e-9, abs=1e-12)
+
+
+def test_single_node_periodic_axis():
+    p = dict(BASE, g_axis=0, bc_lo=(WALL, PER, 0), bc_hi=(WALL, PER, 0))
+    f = case_fields("D2Q9", (40, 1), seed=2)
+    got, ref, _, _ = run_pair("D2Q9", (40, 1), p, f, 50, "fp64")
+    assert_parity(got, ref, "fp64", "ny=1")
+
+
+def test_column1d_full_config_fp64():
+    """The 1D column workload at full size: N = 512, 10,000 steps, FP64."""
+    w = lbm_inputs.WORKLOADS["column1d"]
+    f = lbm_inputs.fields_for("column1d")
+    po = oparams.lattice_params(w["physics"])
+    pl = lparams.lattice_params(w["physics"])
+    o = oracle.Oracle("D1Q3", w["dims"], po)
+    o.init(**f)
+    o.step(w["steps"])
+    ref = o.moments()
+    s = lbm.Simulation("D1Q3", w["dims"], dict(pl, precision="fp64"))
+    s.init(**f)
+    s.step(w["steps"])
+    assert_parity(s.moments(), ref, "fp64", "column1d")
+
+
+def test_box2d_full_size_first_steps_fp32():
+    """The 2D box at its full 512 x 2048 size and in the benchmark's launch
+    configuration, a few steps against the oracle (multi-threaded)."""
+    w = lbm_inputs.WORKLOADS["box2d"]
+    f = lbm_inputs.fields_for("box2d")
+    po = oparams.lattice_params(w["physics"])
+    pl = lparams.lattice_params(w["physics"], precision="fp32")
+    o = oracle.Oracle("D2Q9", w["dims"], po, threads=16)
+    o.init(**f)
+    o.step(5)
+    s = lbm.Simulation("D2Q9", w["dims"], pl)
+    s.init(**f)
+    s.step(5)
+    assert_parity(s.moments(), o.moments(), "fp32", "box2d full")
+
+
+def test_errors_are_reported():
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation("D2Q9", (8, 8), dict(BASE, omega_g=2.5))
+    with pytest.raises(lbm.LBMError):  # inlet only on the low face of g_axis
+        lbm.Simulation("D2Q9", (8, 8), dict(BASE, g_axis=1, bc_lo=(PER, WALL, 0), bc_hi=(PER, INLET, 0)))
+    s = lbm.Simulation("D2Q9", (8, 8), BASE)
+    with pytest.raises(lbm.LBMError) as e:
+        s.step(1)
+    assert e.value.code == -7

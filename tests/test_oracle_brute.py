@@ -7,6 +7,8 @@ contraction code, streaming direction (push vs pull) and precision (FP64 vs
 strip of Table 1, the outlet of Table 2, both drag models, the D = 1 and
 D >= 2 stress forms (psi != 0), the lag latch and every Spalding mode.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -52,7 +54,7 @@ def test_oracle_matches_bruteforce(name):
     D = oracle.LATTICE_D[lat]
     p = dict(oracle.PARAM_DEFAULTS)
     p.update(c["p"])
-    f = _fields(D, dims, seed=hash(name) % 1000)
+    f = _fields(D, dims, seed=zlib.crc32(name.encode()) % 1000)
     o = oracle.Oracle(lat, dims, p)
     o.init(**f)
     b = brute.Brute(D, dims, p)
