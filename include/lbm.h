@@ -41,10 +41,17 @@ enum {
 
 enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2, LBM_D3Q19 = 3 };
 
-/* Storage/arithmetic of the populations.  FP64: double store and math.
- * FP32: float store of the deviations f - w_q*r_s and float math.
- * FP16DEV: half store of the same deviations, float math. */
-enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2 };
+/* Storage/arithmetic of the populations.
+ * FP64: the reference path -- full populations in double, every formula of
+ *   the paper evaluated literally in the order it is written, without
+ *   floating-point contraction (bitwise reproducible against any other such
+ *   evaluation, e.g. a CPU one).
+ * FP32: float store of the deviations f - w_q*r_s (r = 1, or the mean alpha
+ *   for the alpha schemes) and float arithmetic written in those deviations.
+ * FP16DEV: half store of the same deviations, float arithmetic.
+ * FP64DEV: the FP32 kernel's deviation arithmetic in double (validation of
+ *   the fast path's algebra at double precision). */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_FP64DEV = 3 };
 
 /* Face conditions.  WALL: half-way bounce-back for all six schemes (Eq.
  * (BCINLET), BB rule with zero wall velocity).  INLET: Table 1, only on the
@@ -84,7 +91,7 @@ typedef struct {
   int ramp_nt;               /* n_t of Eq. (transient); <= 0: the max at once */
   int inlet_ul_mode;         /* 0: u_l^IN ramp; 1: u_l^IN = -a u_g^IN/(1-a)
                                 (zero net volume flux through the strip) */
-  int precision;             /* LBM_FP64 / LBM_FP32 / LBM_FP16DEV */
+  int precision;             /* LBM_FP64 / LBM_FP32 / LBM_FP16DEV / LBM_FP64DEV */
   int diag_every;            /* > 0: FP64 diagnostics every that many steps
                                 inside lbm_step, checked for NaN / drift */
   double drift_limit;        /* relative drift of sum(a_g) that raises

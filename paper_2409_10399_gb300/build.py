@@ -12,7 +12,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["lbm_capi.cu", "lbm_d1q3.cu", "lbm_d2q9.cu", "lbm_d3q19.cu"]
+SOURCES = ["lbm_capi.cu", "lbm_d1q3.cu", "lbm_d2q9.cu", "lbm_d3q19.cu",
+           "lbm_ref_d1q3.cu", "lbm_ref_d2q9.cu", "lbm_ref_d3q19.cu"]
+# the FP64 reference path is compiled without floating-point contraction
+PER_FILE_FLAGS = {"lbm_ref_d1q3.cu": ["-fmad=false"], "lbm_ref_d2q9.cu": ["-fmad=false"],
+                  "lbm_ref_d3q19.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
@@ -41,7 +45,8 @@ def build(force=False, verbose=False, extra_flags=()):
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + PER_FILE_FLAGS.get(src, []) + list(extra_flags) + \
+            ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -13,6 +13,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_ref.cuh"
 
 namespace lbm {
 cudaError_t launch_step_1(int, const StepArgs &, dim3, dim3, size_t, cudaStream_t);
@@ -30,6 +31,18 @@ cudaError_t launch_init_2(int, const MomArgs &, const double *, const double *, 
                           unsigned, cudaStream_t);
 cudaError_t launch_init_3(int, const MomArgs &, const double *, const double *, const double *, const double *,
                           unsigned, cudaStream_t);
+cudaError_t launch_ref_step_1(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_ref_step_2(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_ref_step_3(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
+cudaError_t launch_ref_moments_1(const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_ref_moments_2(const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_ref_moments_3(const MomArgs &, int, unsigned, cudaStream_t);
+cudaError_t launch_ref_init_1(const MomArgs &, const double *, const double *, const double *, const double *,
+                              unsigned, cudaStream_t);
+cudaError_t launch_ref_init_2(const MomArgs &, const double *, const double *, const double *, const double *,
+                              unsigned, cudaStream_t);
+cudaError_t launch_ref_init_3(const MomArgs &, const double *, const double *, const double *, const double *,
+                              unsigned, cudaStream_t);
 
 __global__ void k_diag_final(const double *partials, int nblocks, double *out) {
   // One warp per diagnostic, each lane sums a fixed strided subset, then a
@@ -91,18 +104,30 @@ static int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return set_err((c), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-static size_t store_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
-static size_t held_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+static size_t store_size(int prec) {
+  return (prec == LBM_FP64 || prec == LBM_FP64DEV) ? 8 : (prec == LBM_FP32 ? 4 : 2);
+}
+static size_t held_size(int prec) { return (prec == LBM_FP64 || prec == LBM_FP64DEV) ? 8 : 4; }
 
 static cudaError_t dispatch_step(lbm_ctx *c, const StepArgs &a) {
   dim3 g(c->grid[0], c->grid[1], c->grid[2]), b(c->T[0], c->T[1], c->T[2]);
   c->launches++;
+  if (c->prec == LBM_FP64) {
+    if (c->lattice == 1) return launch_ref_step_1(a, g, b, c->smem, c->stream);
+    if (c->lattice == 2) return launch_ref_step_2(a, g, b, c->smem, c->stream);
+    return launch_ref_step_3(a, g, b, c->smem, c->stream);
+  }
   if (c->lattice == 1) return launch_step_1(c->prec, a, g, b, c->smem, c->stream);
   if (c->lattice == 2) return launch_step_2(c->prec, a, g, b, c->smem, c->stream);
   return launch_step_3(c->prec, a, g, b, c->smem, c->stream);
 }
 static cudaError_t dispatch_moments(lbm_ctx *c, const MomArgs &ma, int mode) {
   c->launches++;
+  if (c->prec == LBM_FP64) {
+    if (c->lattice == 1) return launch_ref_moments_1(ma, mode, c->nblk_flat, c->stream);
+    if (c->lattice == 2) return launch_ref_moments_2(ma, mode, c->nblk_flat, c->stream);
+    return launch_ref_moments_3(ma, mode, c->nblk_flat, c->stream);
+  }
   if (c->lattice == 1) return launch_moments_1(c->prec, ma, mode, c->nblk_flat, c->stream);
   if (c->lattice == 2) return launch_moments_2(c->prec, ma, mode, c->nblk_flat, c->stream);
   return launch_moments_3(c->prec, ma, mode, c->nblk_flat, c->stream);
@@ -116,6 +141,11 @@ static cudaError_t dispatch_pops(lbm_ctx *c, const MomArgs &ma, int s) {
 static cudaError_t dispatch_init(lbm_ctx *c, const MomArgs &ma, const double *a, const double *ug, const double *ul,
                                  const double *pk) {
   c->launches++;
+  if (c->prec == LBM_FP64) {
+    if (c->lattice == 1) return launch_ref_init_1(ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+    if (c->lattice == 2) return launch_ref_init_2(ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+    return launch_ref_init_3(ma, a, ug, ul, pk, c->nblk_flat, c->stream);
+  }
   if (c->lattice == 1) return launch_init_1(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
   if (c->lattice == 2) return launch_init_2(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
   return launch_init_3(c->prec, ma, a, ug, ul, pk, c->nblk_flat, c->stream);
@@ -190,6 +220,11 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.aIN = ramp(p.in_alpha, t, p.ramp_nt);
   a.ugIN = ramp(p.in_ug, t, p.ramp_nt);
   a.ulIN = p.inlet_ul_mode == 1 ? -a.aIN * a.ugIN / (1.0 - a.aIN) : ramp(p.in_ul, t, p.ramp_nt);
+  a.plain = c->prec == LBM_FP64;
+  a.cs2 = CS2;
+  a.two_cs4 = 2.0 * CS2 * CS2;
+  a.nuef_g = (1.0 / p.omega_g - 0.5) - CS2 * p.psi_g / p.omega_g;
+  a.nuef_l = (1.0 / p.omega_l - 0.5) - CS2 * p.psi_l / p.omega_l;
   return a;
 }
 
@@ -237,7 +272,8 @@ static int choose_tiles(lbm_ctx *c) {
     }
     if (s < 0) return set_err(c, LBM_EINVAL, "no tile shift keeps the outlet pair in one block");
     c->shift[ga] = s;
-    c->smem = (size_t)c->T[0] * c->T[1] * c->T[2] * XCH * (c->prec == LBM_FP64 ? 8 : 4);
+    const size_t per = c->prec == LBM_FP64 ? RXCH * 8 : (c->prec == LBM_FP64DEV ? XCH * 8 : XCH * 4);
+    c->smem = (size_t)c->T[0] * c->T[1] * c->T[2] * per;
   } else {
     c->smem = 0;
   }
@@ -282,7 +318,7 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   const lbm_params &q = *p;
   if (!(q.R >= 1.0) || !(q.omega_g > 0 && q.omega_g < 2) || !(q.omega_l > 0 && q.omega_l < 2) ||
       !(q.omega_alpha > 0 && q.omega_alpha < 2) || q.n_gamma < 1 || q.spalding_mode < 0 || q.spalding_mode > 2 ||
-      !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 2 ||
+      !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 3 ||
       (q.drag_model != LBM_DRAG_CONST && q.drag_model != LBM_DRAG_CGW) || q.diag_every < 0)
     return LBM_EINVAL;
   int dims[3] = {nx, ny, nz};

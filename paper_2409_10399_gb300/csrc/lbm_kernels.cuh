@@ -53,6 +53,9 @@ struct StepArgs {
   int cgw, spalding;
   double r_ag, r_al;                                 // deviation references of f_alpha
   double aIN, ugIN, ulIN;                            // inlet values at this t, Eq. (transient)
+  // reference (FP64, full-population) path
+  int plain;                                         // store holds full f, not deviations
+  double cs2, two_cs4, nuef_g, nuef_l;               // 1/3, 2 cs2 cs2, nu_ef of Eq. (lbm-ef-viscosity)
 };
 
 // ------------------------------------------------------------ store access
@@ -157,7 +160,7 @@ __device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, 
     plane_q = q;
     return g.node;
   }
-  plane_q = opp_of(q);
+  plane_q = L::opp(q);
   return shifted_node<L>(a, g, q, -1);
 }
 
@@ -165,7 +168,7 @@ __device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, 
 template <class L>
 __device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g, int q, bool cross, int &plane_q) {
   if (a.parity == 0 || cross) {
-    plane_q = opp_of(q);
+    plane_q = L::opp(q);
     return g.node;
   }
   plane_q = q;
@@ -266,12 +269,14 @@ __device__ __forceinline__ R vdot(int q, const R u[3]) {
   return s;
 }
 
-// f^eq(alpha, u)_q - w_q*r with the quadratic term of Eq. (equilibrium).
+// f^eq(alpha, u)_q - w_q*r with the quadratic term of Eq. (equilibrium),
+// grouped as w [(alpha - r) + alpha (3 v.u + 9/2 (v.u)^2 - 3/2 u^2)] so that
+// alpha = r (the beta schemes, r = 1) loses nothing to cancellation.
 template <class L, class R>
 __device__ __forceinline__ R feqS_dev(int q, R alpha, const R u[3], R uu, R r) {
   const R w = (R)L::w(q);
   const R vu = vdot<L, R>(q, u);
-  return w * (alpha * (R(1) + R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu) - r);
+  return w * ((alpha - r) + alpha * (R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu));
 }
 
 // Values a face rule streams back into the node, as deviations.  xn holds the
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
     const bool cross = crosses<L>(g, q, +1);
     if (cross) {
       const int rule = face_rule<L>(a, g, q);
-      const int qo = opp_of(q);
+      const int qo = L::opp(q);
       if (rule == BC_INLET) {
         // Table 1: f_g, f_l BB(I) (Eq. (BB): -2 w v.u^B/cs2), f_alpha EQ(S)
         // Dirichlet, f_beta EQ(S) with beta and c extrapolated full-way.
@@ -508,8 +513,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
         out[1] = -out[1] + R(2) * w * ql;
         const R abg = R(1.5) * m.alg - R(0.5) * xn[6];
         const R abl = R(1.5) * m.all - R(0.5) * xn[7];
-        out[2] = -out[2] - R(2) * w * rag + R(2) * w * abg * (R(1) + qg);
-        out[3] = -out[3] - R(2) * w * ral + R(2) * w * abl * (R(1) + ql);
+        out[2] = -out[2] + R(2) * w * ((abg - rag) + abg * qg);
+        out[3] = -out[3] + R(2) * w * ((abl - ral) + abl * ql);
         out[4] = feqS_dev<L, R>(qo, R(1), cb, cb2, R(1));
         out[5] = feqS_dev<L, R>(qo, R(1), cc, cc2, R(1));
       }
@@ -545,9 +550,30 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// One thread per node over a flat 1D grid (block 256); FP64 block reduction
-// of the eight diagnostics: warp shuffles, then one value per warp in shared
-// memory, then warp 0.
+// FP64 block reduction of the eight diagnostics (block of 256 threads): warp
+// shuffles, one value per warp in shared memory, then warp 0 writes the
+// block's partial (slot 4 is a maximum, the others sums).
+__device__ __forceinline__ void block_diag_reduce(double v[8], double *partials) {
+  __shared__ double red[8][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; k++) v[k] = (k == 4) ? warp_max(v[k]) : warp_sum<double>(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 8; k++) red[k][wid] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      double x = lane < nw ? red[k][lane] : 0.0;
+      x = (k == 4) ? warp_max(x) : warp_sum<double>(x);
+      if (lane == 0) partials[(long long)blockIdx.x * 8 + k] = x;
+    }
+  }
+}
+
+// One thread per node over a flat 1D grid (block 256).
 template <class L, class S, class R>
 __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
   constexpr int D = L::D, Q = L::Q;
@@ -598,25 +624,7 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
       v[7] = m.del;
     }
   }
-  if (mode & 2) {
-    __shared__ double red[8][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 8; k++) v[k] = (k == 4) ? warp_max(v[k]) : warp_sum<R>(v[k]);
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 8; k++) red[k][wid] = v[k];
-    __syncthreads();
-    if (wid == 0) {
-      const int nw = blockDim.x >> 5;
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        double x = lane < nw ? red[k][lane] : (k == 4 ? 0.0 : 0.0);
-        x = (k == 4) ? warp_max(x) : warp_sum<R>(x);
-        if (lane == 0) ma.partials[(long long)blockIdx.x * 8 + k] = x;
-      }
-    }
-  }
+  if (mode & 2) block_diag_reduce(v, ma.partials);
 }
 
 // Final pass of the diagnostics: one block sums the per-block partials in a
@@ -636,13 +644,13 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
   g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
   make_geo(a, D, g);
   const S *base = (const S *)a.pop;
-  const double r = s == 2 ? a.r_ag : (s == 3 ? a.r_al : 1.0);
+  const double r = a.plain ? 0.0 : (s == 2 ? a.r_ag : (s == 3 ? a.r_al : 1.0));
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     int pq;
     long long idx = read_slot<L>(a, g, q, pq);
     double dv = Store<S>::template ld<double>(base + (long long)(s * Q + pq) * a.plane + idx);
-    ma.out[(long long)q * ma.N + i] = dv + L::w(q) * r;
+    ma.out[(long long)q * ma.N + i] = a.plain ? dv : dv + L::w(q) * r;
   }
 }
 

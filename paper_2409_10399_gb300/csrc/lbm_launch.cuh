@@ -10,27 +10,29 @@ namespace lbm {
 template <int LAT>
 struct Launch {
   using L = Lattice<LAT>;
+  // prec: 1 = FP32, 2 = FP16 store, 3 = FP64 deviations (0, the FP64
+  // reference path, has its own launchers in lbm_ref_*.cu)
   static cudaError_t step(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    if (prec == 0) k_step<L, double, double><<<grid, block, smem, st>>>(a);
+    if (prec == 3) k_step<L, double, double><<<grid, block, smem, st>>>(a);
     else if (prec == 1) k_step<L, float, float><<<grid, block, smem, st>>>(a);
     else k_step<L, __half, float><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t moments(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
-    if (prec == 0) k_moments<L, double, double><<<nblk, 256, 0, st>>>(ma, mode);
+    if (prec == 3) k_moments<L, double, double><<<nblk, 256, 0, st>>>(ma, mode);
     else if (prec == 1) k_moments<L, float, float><<<nblk, 256, 0, st>>>(ma, mode);
     else k_moments<L, __half, float><<<nblk, 256, 0, st>>>(ma, mode);
     return cudaGetLastError();
   }
   static cudaError_t pops(int prec, const MomArgs &ma, int s, unsigned nblk, cudaStream_t st) {
-    if (prec == 0) k_pops<L, double, double><<<nblk, 256, 0, st>>>(ma, s);
+    if (prec == 0 || prec == 3) k_pops<L, double, double><<<nblk, 256, 0, st>>>(ma, s);
     else if (prec == 1) k_pops<L, float, float><<<nblk, 256, 0, st>>>(ma, s);
     else k_pops<L, __half, float><<<nblk, 256, 0, st>>>(ma, s);
     return cudaGetLastError();
   }
   static cudaError_t init(int prec, const MomArgs &ma, const double *a, const double *ug, const double *ul,
                           const double *pk, unsigned nblk, cudaStream_t st) {
-    if (prec == 0) k_init<L, double><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    if (prec == 3) k_init<L, double><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
     else if (prec == 1) k_init<L, float><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
     else k_init<L, __half><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
     return cudaGetLastError();

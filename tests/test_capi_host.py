@@ -48,9 +48,13 @@ def test_lattice_tables_match_oracle(lat):
     ref = {tuple(r): x for r, x in zip(vo.tolist(), wo)}
     assert mine == ref
     assert np.all(v[0] == 0)
-    # opposite directions adjacent: opp(q) = q+1 for odd q
-    for q in range(1, len(w), 2):
-        assert np.all(v[q] == -v[q + 1])
+    # lexicographic order of the moving velocities, so opp(q) = Q - q
+    Q = len(w)
+    for q in range(1, Q):
+        assert np.all(v[q] == -v[Q - q])
+    assert [tuple(r) for r in v[1:].tolist()] == sorted(tuple(r) for r in v[1:].tolist())
+    # same order as the oracle's own construction (bitwise FP64 parity sums moments in this order)
+    assert np.array_equal(v, vo) and np.array_equal(w, wo)
 
 
 def test_invalid_lattice_rejected_without_gpu():
