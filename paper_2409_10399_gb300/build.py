@@ -19,6 +19,7 @@ PER_FILE_FLAGS = {"lbm_ref_d1q3.cu": ["-fmad=false"], "lbm_ref_d2q9.cu": ["-fmad
                   "lbm_ref_d3q19.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 
 
