@@ -158,6 +158,16 @@ int lbm_get_diag(lbm_ctx *c, double out[8]);
  * the legacy default stream.  The caller keeps the stream alive. */
 int lbm_set_stream(lbm_ctx *c, void *cuda_stream);
 
+/* Thread-block tile of the fused step kernel, tx*ty*tz threads over
+ * (x, y, z), tx*ty*tz <= 256 and a multiple of 32.  The default is chosen at
+ * lbm_create; an autotuner may try others.  With an inlet or outlet face the
+ * tile along g_axis must be >= 2 (LBM_EINVAL otherwise).  Takes effect at the
+ * next lbm_step; results do not depend on the tile. */
+int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz);
+
+/* Current tile (tile[0..2]) of the fused step kernel. */
+int lbm_get_tile(const lbm_ctx *c, int tile[3]);
+
 /* Time step counter t (number of completed steps since lbm_init). */
 int lbm_time(const lbm_ctx *c, long long *t);
 

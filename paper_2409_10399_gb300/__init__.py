@@ -77,6 +77,8 @@ def load_library(build_if_missing=True):
             "lbm_get_diag": (I, [P, ctypes.POINTER(D)]),
             "lbm_set_stream": (I, [P, P]),
             "lbm_time": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_set_tile": (I, [P, I, I, I]),
+            "lbm_get_tile": (I, [P, ctypes.POINTER(I)]),
             "lbm_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_last_error": (ctypes.c_char_p, [P]),
             "lbm_destroy": (I, [P]),
@@ -199,6 +201,16 @@ class Simulation:
 
     def step(self, n=1):
         self._check(self._lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    def set_tile(self, tx, ty=1, tz=1):
+        """Thread-block tile of the fused step (results do not depend on it)."""
+        self._check(self._lib.lbm_set_tile(self._h, int(tx), int(ty), int(tz)), "lbm_set_tile")
+
+    @property
+    def tile(self):
+        t = (ctypes.c_int * 3)()
+        self._check(self._lib.lbm_get_tile(self._h, t), "lbm_get_tile")
+        return tuple(t)
 
     @property
     def t(self):

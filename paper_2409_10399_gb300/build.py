@@ -14,9 +14,12 @@ SO = os.path.join(BUILD, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["lbm_capi.cu", "lbm_d1q3.cu", "lbm_d2q9.cu", "lbm_d3q19.cu",
            "lbm_ref_d1q3.cu", "lbm_ref_d2q9.cu", "lbm_ref_d3q19.cu"]
-# the FP64 reference path is compiled without floating-point contraction
+# the FP64 reference path is compiled without floating-point contraction;
+# the fast paths use approximate single-precision division and square root
+FAST = ["-prec-div=false", "-prec-sqrt=false"]
 PER_FILE_FLAGS = {"lbm_ref_d1q3.cu": ["-fmad=false"], "lbm_ref_d2q9.cu": ["-fmad=false"],
-                  "lbm_ref_d3q19.cu": ["-fmad=false"]}
+                  "lbm_ref_d3q19.cu": ["-fmad=false"], "lbm_d1q3.cu": FAST, "lbm_d2q9.cu": FAST,
+                  "lbm_d3q19.cu": FAST}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-Xcompiler", "-ffp-contract=off",

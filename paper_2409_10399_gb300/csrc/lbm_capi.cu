@@ -221,6 +221,21 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.ugIN = ramp(p.in_ug, t, p.ramp_nt);
   a.ulIN = p.inlet_ul_mode == 1 ? -a.aIN * a.ugIN / (1.0 - a.aIN) : ramp(p.in_ul, t, p.ramp_nt);
   a.plain = c->prec == LBM_FP64;
+  // the same constants in the kernels' arithmetic types
+  PhysT<double> &d = a.pd;
+  d.R_ = a.R; d.invR = a.invR; d.omega_g = a.omega_g; d.omega_l = a.omega_l; d.omega_a = a.omega_a;
+  d.kgrad = a.kgrad; d.A_g = a.A_g; d.B_g = a.B_g; d.A_l = a.A_l; d.B_l = a.B_l; d.eta0_g = a.eta0_g;
+  d.eta0_l = a.eta0_l; d.psi_g = a.psi_g; d.psi_l = a.psi_l; d.k0 = a.k0; d.kappa_I = a.kappa_I;
+  d.kappa_W = a.kappa_W; d.buoy = a.buoy; d.gamma = a.gamma; d.afloor = a.afloor; d.r_ag = a.r_ag;
+  d.r_al = a.r_al; d.aIN = a.aIN; d.ugIN = a.ugIN; d.ulIN = a.ulIN;
+  PhysT<float> &f = a.pf;
+  f.R_ = (float)d.R_; f.invR = (float)d.invR; f.omega_g = (float)d.omega_g; f.omega_l = (float)d.omega_l;
+  f.omega_a = (float)d.omega_a; f.kgrad = (float)d.kgrad; f.A_g = (float)d.A_g; f.B_g = (float)d.B_g;
+  f.A_l = (float)d.A_l; f.B_l = (float)d.B_l; f.eta0_g = (float)d.eta0_g; f.eta0_l = (float)d.eta0_l;
+  f.psi_g = (float)d.psi_g; f.psi_l = (float)d.psi_l; f.k0 = (float)d.k0; f.kappa_I = (float)d.kappa_I;
+  f.kappa_W = (float)d.kappa_W; f.buoy = (float)d.buoy; f.gamma = (float)d.gamma; f.afloor = (float)d.afloor;
+  f.r_ag = (float)d.r_ag; f.r_al = (float)d.r_al; f.aIN = (float)d.aIN; f.ugIN = (float)d.ugIN;
+  f.ulIN = (float)d.ulIN;
   a.cs2 = CS2;
   a.two_cs4 = 2.0 * CS2 * CS2;
   a.nuef_g = (1.0 / p.omega_g - 0.5) - CS2 * p.psi_g / p.omega_g;
@@ -251,9 +266,9 @@ static int ensure_stage(lbm_ctx *c, size_t bytes) {
 }
 
 // Tile of the fused kernel: x fastest; the axis of the inlet/outlet faces
-// gets a tile of at least 4 and a shift so that each edge node and its inward
+// gets a tile of at least 2 and a shift so that each edge node and its inward
 // neighbour share a block (their values are exchanged in shared memory).
-static int choose_tiles(lbm_ctx *c) {
+static void default_tile(lbm_ctx *c) {
   const lbm_params &p = c->p;
   if (c->D == 1) { c->T[0] = 128; c->T[1] = 1; c->T[2] = 1; }
   else if (c->D == 2) { c->T[0] = 64; c->T[1] = 4; c->T[2] = 1; }
@@ -261,6 +276,13 @@ static int choose_tiles(lbm_ctx *c) {
   const int ga = p.g_axis;
   const int io = (p.bc_lo[ga] == LBM_BC_INLET) || (p.bc_hi[ga] == LBM_BC_OUTLET);
   if (io && c->D == 3 && ga == 2) { c->T[1] = 2; c->T[2] = 4; }
+}
+
+static int choose_tiles(lbm_ctx *c) {
+  const lbm_params &p = c->p;
+  const int ga = p.g_axis;
+  const int io = (p.bc_lo[ga] == LBM_BC_INLET) || (p.bc_hi[ga] == LBM_BC_OUTLET);
+  if (io && c->T[ga] < 2) return set_err(c, LBM_EINVAL, "tile along g_axis must be >= 2 with an inlet/outlet");
   for (int d = 0; d < 3; d++) c->shift[d] = 0;
   if (io) {
     const int T = c->T[ga], n = c->n[ga];
@@ -314,7 +336,7 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   if (!p) return LBM_EINVAL;
   if (lattice < 1 || lattice > 3 || dim != lattice) return LBM_EINVAL;
   if (nx < 1 || ny < 1 || nz < 1 || (dim < 2 && ny != 1) || (dim < 3 && nz != 1)) return LBM_EINVAL;
-  if ((long long)nx * ny * nz > (1LL << 34)) return LBM_EINVAL;
+  if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_EINVAL;  // 32-bit node indices
   const lbm_params &q = *p;
   if (!(q.R >= 1.0) || !(q.omega_g > 0 && q.omega_g < 2) || !(q.omega_l > 0 && q.omega_l < 2) ||
       !(q.omega_alpha > 0 && q.omega_alpha < 2) || q.n_gamma < 1 || q.spalding_mode < 0 || q.spalding_mode > 2 ||
@@ -347,6 +369,7 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   c->plane = (c->N + 63) / 64 * 64;  // 256-byte aligned planes for every store type
   c->p = q;
   c->nblk_flat = (unsigned)((c->N + 255) / 256);
+  default_tile(c);
   int rc = choose_tiles(c);
   if (rc) { int e = rc; delete c; return e; }
   size_t pop_bytes = (size_t)6 * c->Q * c->plane * store_size(c->prec);
@@ -522,6 +545,30 @@ int lbm_get_diag(lbm_ctx *c, double out[8]) {
   if (rc) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(out, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz) {
+  if (!c) return LBM_EINVAL;
+  const int n = tx * ty * tz;
+  if (tx < 1 || ty < 1 || tz < 1 || n > 256 || n % 32 != 0 || (c->D < 2 && ty != 1) || (c->D < 3 && tz != 1))
+    return set_err(c, LBM_EINVAL, "invalid tile %dx%dx%d", tx, ty, tz);
+  int old[3] = {c->T[0], c->T[1], c->T[2]};
+  c->T[0] = tx;
+  c->T[1] = ty;
+  c->T[2] = tz;
+  int rc = choose_tiles(c);
+  if (rc) {
+    for (int d = 0; d < 3; d++) c->T[d] = old[d];
+    choose_tiles(c);
+    return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_get_tile(const lbm_ctx *c, int tile[3]) {
+  if (!c || !tile) return LBM_EINVAL;
+  for (int d = 0; d < 3; d++) tile[d] = c->T[d];
   return LBM_OK;
 }
 

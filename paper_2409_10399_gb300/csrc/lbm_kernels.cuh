@@ -29,8 +29,18 @@ namespace lbm {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
 
-// Per-launch arguments.  Physics constants are precomputed on the host in
-// double; each kernel converts them to its arithmetic type once.
+// Physics constants of one launch in the kernel's arithmetic type, so that no
+// thread converts from double (FP64 units are scarce on this GPU).
+template <class R> struct PhysT {
+  R R_, invR, omega_g, omega_l, omega_a, kgrad;  // kgrad = omega_alpha / cs2
+  R A_g, B_g, A_l, B_l;                          // sigma = A (Pi^eq - Pi) + B S'' I
+  R eta0_g, eta0_l, psi_g, psi_l, k0;            // eta_q(psi) rest / moving; (1-w0)/w0
+  R kappa_I, kappa_W, buoy, gamma, afloor;
+  R r_ag, r_al;                                  // deviation references of f_alpha
+  R aIN, ugIN, ulIN;                             // inlet values at this t
+};
+
+// Per-launch arguments (everything the fused step and the moment kernels need).
 struct StepArgs {
   void *pop;            // 6*Q planes of the store type
   void *held;           // 3 planes: S''_g, S''_l, Lambda' (float, or double for FP64)
@@ -56,7 +66,13 @@ struct StepArgs {
   // reference (FP64, full-population) path
   int plain;                                         // store holds full f, not deviations
   double cs2, two_cs4, nuef_g, nuef_l;               // 1/3, 2 cs2 cs2, nu_ef of Eq. (lbm-ef-viscosity)
+  PhysT<float> pf;                                   // the constants above, pre-converted
+  PhysT<double> pd;
 };
+
+template <class R> __device__ __forceinline__ const PhysT<R> &phys(const StepArgs &a);
+template <> __device__ __forceinline__ const PhysT<float> &phys<float>(const StepArgs &a) { return a.pf; }
+template <> __device__ __forceinline__ const PhysT<double> &phys<double>(const StepArgs &a) { return a.pd; }
 
 // ------------------------------------------------------------ store access
 
@@ -69,52 +85,61 @@ template <> struct Store<float> {
   template <class R> __device__ __forceinline__ static R ld(const float *p) { return (R)__ldg(p); }
   template <class R> __device__ __forceinline__ static void st(float *p, R v) { *p = (float)v; }
 };
+// Half store of deviations scaled by 2^12 (exact): |f - w r| < 1 < 65504/2^12,
+// and deviations down to 1.5e-8 stay normal numbers (11-bit significand)
+// instead of half subnormals (absolute spacing 6e-8).
+constexpr float HALF_SCALE = 4096.0f, HALF_UNSCALE = 1.0f / 4096.0f;
 template <> struct Store<__half> {
   template <class R> __device__ __forceinline__ static R ld(const __half *p) {
-    return (R)__half2float(__ldg(p));
+    return (R)(__half2float(__ldg(p)) * HALF_UNSCALE);
   }
-  template <class R> __device__ __forceinline__ static void st(__half *p, R v) { *p = __float2half_rn((float)v); }
+  template <class R> __device__ __forceinline__ static void st(__half *p, R v) {
+    *p = __float2half_rn((float)v * HALF_SCALE);
+  }
 };
 
-// Node geometry: neighbour coordinates along each axis (with periodic wrap)
-// and whether a step leaves the domain through a non-periodic face.
+// Node geometry: index, offsets (in nodes, 32-bit) of the +1 / -1 neighbour
+// along each axis with periodic wrap, and whether a step leaves the domain
+// through a non-periodic face.  The library keeps N < 2^31.
 struct Geo {
   int c[3];
-  int p[3], m[3];        // coordinate of +1 / -1 neighbour (wrapped)
+  int op[3], om[3];      // node offset of the +1 / -1 neighbour (wrapped)
   bool xp[3], xm[3];     // +1 / -1 step crosses a non-periodic face
-  long long node;
+  int node;
 };
 
 __device__ __forceinline__ void make_geo(const StepArgs &a, int D, Geo &g) {
+  int stride = 1;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    int n = a.n[d], c = g.c[d];
-    g.p[d] = c + 1;
-    g.m[d] = c - 1;
+    const int n = a.n[d], c = g.c[d];
+    g.op[d] = stride;
+    g.om[d] = -stride;
     g.xp[d] = false;
     g.xm[d] = false;
     if (d < D) {
-      if (g.p[d] >= n) {
-        if (a.bc_hi[d] == BC_PERIODIC) g.p[d] = 0; else g.xp[d] = true;
+      if (c + 1 >= n) {
+        if (a.bc_hi[d] == BC_PERIODIC) g.op[d] = -(n - 1) * stride; else g.xp[d] = true;
       }
-      if (g.m[d] < 0) {
-        if (a.bc_lo[d] == BC_PERIODIC) g.m[d] = n - 1; else g.xm[d] = true;
+      if (c == 0) {
+        if (a.bc_lo[d] == BC_PERIODIC) g.om[d] = (n - 1) * stride; else g.xm[d] = true;
       }
     }
+    stride *= n;
   }
-  g.node = (long long)g.c[0] + (long long)a.n[0] * ((long long)g.c[1] + (long long)a.n[1] * g.c[2]);
+  g.node = g.c[0] + a.n[0] * (g.c[1] + a.n[1] * g.c[2]);
 }
 
 template <class L>
 __device__ __forceinline__ long long shifted_node(const StepArgs &a, const Geo &g, int q, int sign) {
   // node index of x + sign*v_q with periodic wrap (only valid if not crossing)
-  int cc[3];
+  int idx = g.node;
 #pragma unroll
-  for (int d = 0; d < 3; d++) {
-    int vv = sign * L::v(q, d);
-    cc[d] = vv > 0 ? g.p[d] : (vv < 0 ? g.m[d] : g.c[d]);
+  for (int d = 0; d < L::D; d++) {
+    const int vv = sign * L::v(q, d);
+    idx += vv > 0 ? g.op[d] : (vv < 0 ? g.om[d] : 0);
   }
-  return (long long)cc[0] + (long long)a.n[0] * ((long long)cc[1] + (long long)a.n[1] * cc[2]);
+  return idx;
 }
 
 template <class L>
@@ -206,6 +231,7 @@ __host__ __device__ constexpr int pidx(int a, int b) {
 template <class L, class R>
 __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], Moments<L, R> &m) {
   constexpr int D = L::D;
+  const PhysT<R> &P = phys<R>(a);
   m.deg = m.del = m.ag = m.al = m.Sg = m.Sl = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) m.ug[d] = m.ul[d] = m.Jg[d] = m.Jl[d] = R(0);
@@ -240,8 +266,8 @@ __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], M
       }
     }
   }
-  m.ag += (R)a.r_ag;
-  m.al += (R)a.r_al;
+  m.ag += P.r_ag;
+  m.al += P.r_al;
   if (a.spalding == 0) {
     m.alg = m.ag;
     m.all = m.al;
@@ -335,7 +361,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   }
   if (!active) return;
 
-  const R R_ = (R)a.R, invR = (R)a.invR;
+  const PhysT<R> &P = phys<R>(a);
+  const R R_ = P.R_, invR = P.invR;
   // ---- sources: Eq. (lbmbetataylorzeroth5), dashpot Eqs. (lbm-cont-g1Dhat),
   //      (lbm-cont-l1Dhat) third strategy with phi*eps_l - 1 = (eps_g - 1)/R
   const R dPl = m.deg * invR;
@@ -349,8 +376,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   H *held = (H *)a.held;
   R Spp_g, Spp_l, Lam;
   if (a.latch) {
-    Spp_g = m.Sg - (R)a.gamma * ug2 * m.deg;
-    Spp_l = m.Sl - (R)a.gamma * ul2 * dPl;
+    Spp_g = m.Sg - P.gamma * ug2 * m.deg;
+    Spp_l = m.Sl - P.gamma * ul2 * dPl;
     Lam = m.alg * m.all * (m.alg + m.all * R_);  // Eq. (Lambda)
     held[g.node] = (H)Spp_g;
     held[a.plane + g.node] = (H)Spp_l;
@@ -367,7 +394,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   // ---- grad(alpha): Eq. (gradlnalpha) times alpha, corrected by Eq. (spalding2);
   //      grad^G alpha_l = -grad^G alpha_g
   R gG[3] = {R(0), R(0), R(0)};
-  const R kg = (R)a.kgrad;
+  const R kg = P.kgrad;
 #pragma unroll
   for (int d = 0; d < D; d++) {
     R grg = kg * (m.ag * m.ug[d] - m.Jg[d]);
@@ -389,7 +416,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
         Ng[k] = m.ug[d] * m.ug[e] - m.Pg[k] + (d == e ? cs2 * m.deg : R(0));
         Nl[k] = m.ul[d] * m.ul[e] - m.Pl[k] + (d == e ? cs2 * dPl : R(0));
       }
-    const R Ag = (R)a.A_g, Al = (R)a.A_l, Bg = (R)a.B_g * Spp_g, Bl = (R)a.B_l * Spp_l;
+    const R Ag = P.A_g, Al = P.A_l, Bg = P.B_g * Spp_g, Bl = P.B_l * Spp_l;
 #pragma unroll
     for (int d = 0; d < D; d++) {
       R sg = Bg * gG[d], sl = -Bl * gG[d];
@@ -408,8 +435,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   //      friction (Eq. (wallmomentum1D)), forces Eqs. (Gg), (Gl), (Gg1D)
   R Gg[3] = {R(0), R(0), R(0)}, Gl[3] = {R(0), R(0), R(0)};
   {
-    const R KI = a.cgw ? (R)a.kappa_I * Lam : (R)a.kappa_I;
-    const R KW = a.cgw ? (R)a.kappa_W * Lam : (R)a.kappa_W;
+    const R KI = a.cgw ? P.kappa_I * Lam : P.kappa_I;
+    const R KW = a.cgw ? P.kappa_W * Lam : P.kappa_W;
     R du[3], du2 = R(0);
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -417,22 +444,22 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
       du2 += du[d] * du[d];
     }
     const R ndu = sqrt(du2), nul = sqrt(ul2);
-    const R fl = (R)a.afloor;
+    const R fl = P.afloor;
     const R inv_g = R(1) / (m.alg > fl ? m.alg : fl);
     const R inv_l = R(1) / (m.all > fl ? m.all : fl);
 #pragma unroll
     for (int d = 0; d < D; d++) {
-      Gg[d] = Spp_g * m.ug[d] + (sgG[d] + KI * ndu * du[d]) * inv_g + (d == a.g_axis ? (R)a.buoy : R(0));
+      Gg[d] = Spp_g * m.ug[d] + (sgG[d] + KI * ndu * du[d]) * inv_g + (d == a.g_axis ? P.buoy : R(0));
       Gl[d] = Spp_l * m.ul[d] + slG[d] * inv_l - (KI * ndu * du[d] + KW * nul * m.ul[d]) * inv_l * invR;
     }
   }
 
   // ---- collisions and AA store with face rules
   S *base = (S *)a.pop;
-  const R om_g = (R)a.omega_g, om_l = (R)a.omega_l, om_a = (R)a.omega_a;
-  const R k0 = (R)a.k0;
+  const R om_g = P.omega_g, om_l = P.omega_l, om_a = P.omega_a;
+  const R k0 = P.k0;
   const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
-  const R rag = (R)a.r_ag, ral = (R)a.r_al;
+  const R rag = P.r_ag, ral = P.r_al;
   R c2g = R(0), c2l = R(0);
 #pragma unroll
   for (int d = 0; d < D; d++) {
@@ -442,8 +469,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
   // equilibrium offsets of f_I^eq - w: rest and moving directions, Eq. (eta)
   const R eI_g0 = m.deg, eI_gq = m.deg;                 // phi_g = 1
   const R eI_l0 = m.del + k0 * (m.del - dPl), eI_lq = dPl;
-  const R eL_g0 = Spp_g * (R)a.eta0_g, eL_gq = Spp_g * (R)a.psi_g;
-  const R eL_l0 = Spp_l * (R)a.eta0_l, eL_lq = Spp_l * (R)a.psi_l;
+  const R eL_g0 = Spp_g * P.eta0_g, eL_gq = Spp_g * P.psi_g;
+  const R eL_l0 = Spp_l * P.eta0_l, eL_lq = Spp_l * P.psi_l;
 
 #pragma unroll
   for (int q = 0; q < Q; q++) {
@@ -468,16 +495,16 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a) {
         // Table 1: f_g, f_l BB(I) (Eq. (BB): -2 w v.u^B/cs2), f_alpha EQ(S)
         // Dirichlet, f_beta EQ(S) with beta and c extrapolated full-way.
         const R vq = (R)(gax == 0 ? L::v(q, 0) : (gax == 1 ? L::v(q, 1) : L::v(q, 2)));
-        out[0] -= R(6) * w * vq * (R)a.ugIN;
-        out[1] -= R(6) * w * vq * (R)a.ulIN;
+        out[0] -= R(6) * w * vq * P.ugIN;
+        out[1] -= R(6) * w * vq * P.ulIN;
         R uin[3], lin[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-          uin[d] = d == gax ? (R)a.ugIN : R(0);
-          lin[d] = d == gax ? (R)a.ulIN : R(0);
+          uin[d] = d == gax ? P.ugIN : R(0);
+          lin[d] = d == gax ? P.ulIN : R(0);
         }
-        out[2] = feqS_dev<L, R>(qo, (R)a.aIN, uin, (R)a.ugIN * (R)a.ugIN, rag);
-        out[3] = feqS_dev<L, R>(qo, R(1) - (R)a.aIN, lin, (R)a.ulIN * (R)a.ulIN, ral);
+        out[2] = feqS_dev<L, R>(qo, P.aIN, uin, P.ugIN * P.ugIN, rag);
+        out[3] = feqS_dev<L, R>(qo, R(1) - P.aIN, lin, P.ulIN * P.ulIN, ral);
         const R *xn = xch + (tid + gstride) * XCH;
         R cb[3] = {R(0), R(0), R(0)}, cc[3] = {R(0), R(0), R(0)}, cb2 = R(0), cc2 = R(0);
 #pragma unroll
