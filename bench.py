@@ -230,7 +230,9 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    # per-kernel timing: an event pair around every SAMPLE-th step kernel
+    SAMPLE = 16
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (K // SAMPLE + 1))]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(torch.cuda.current_device())
     if dist:
@@ -241,10 +243,16 @@ def run_native(args, rank, world, local_rank):
     l0 = sim.launches
     t0_wall = time.perf_counter()
     t_start.record(stream)
-    for k in range(K):
-        ev[2 * k].record(stream)
+    k = 0
+    while k < K:
+        j = k // SAMPLE
+        ev[2 * j].record(stream)
         sim.step(1)
-        ev[2 * k + 1].record(stream)
+        ev[2 * j + 1].record(stream)
+        n = min(SAMPLE - 1, K - k - 1)
+        if n:
+            sim.step(n)
+        k += 1 + n
     t_end.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0_wall
@@ -254,8 +262,8 @@ def run_native(args, rank, world, local_rank):
     launches = sim.launches - l0
     t_total = t_start.elapsed_time(t_end) / 1e3
     t0 = sim.t - K
-    step_times = [ev[2 * k].elapsed_time(ev[2 * k + 1]) / 1e3 for k in range(K)
-                  if (t0 + k + 1) % DIAG_EVERY != 0]
+    step_times = [ev[2 * j].elapsed_time(ev[2 * j + 1]) / 1e3 for j in range((K + SAMPLE - 1) // SAMPLE)
+                  if (t0 + j * SAMPLE + 1) % DIAG_EVERY != 0]
     kern_s = sum(step_times) / len(step_times)
     if dist:
         tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)

@@ -49,10 +49,17 @@ def run_pair(lat, dims, p, fields, steps, prec, threads=8):
 
 
 def assert_parity(got, ref, prec, ctx=""):
+    """alpha_g and p_k: relative L2 per field.  u: relative L2 of the two-phase
+    velocity field (u_g, u_l) taken together -- at R = 1000 the liquid of a
+    closed column is nearly at rest, and a per-phase ratio would measure
+    rounding against a field that is almost zero."""
     tol = TOL[prec]
-    for k in ("alpha_g", "u_g", "u_l", "p_k"):
+    for k in ("alpha_g", "p_k"):
         e = rel(got[k], ref[k])
         assert e <= tol, "%s %s rel L2 %.3e > %.1e" % (ctx, k, e, tol)
+    e = rel(np.concatenate([got["u_g"].ravel(), got["u_l"].ravel()]),
+            np.concatenate([ref["u_g"].ravel(), ref["u_l"].ravel()]))
+    assert e <= tol, "%s u rel L2 %.3e > %.1e" % (ctx, e, tol)
     # S = 1 - beta is a small difference: compare on the scale of max |S|
     for k in ("S_g", "S_l"):
         e = np.abs(got[k] - ref[k]).max()
