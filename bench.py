@@ -308,7 +308,7 @@ def run_native(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else ("f64" if prec == "fp64" else "f16-store/f32"),
         "data": "synthetic",
         "config": {"workload": workload_desc(WORKLOAD), "lattice": lat, "nodes": N, "precision": prec,
-                   "diag_every": DIAG_EVERY, "l2": "store %.0f MB > L2, no flush" % (N * bpn / 2 / 1e6),
+                   "diag_every": DIAG_EVERY, "l2": "store %.0f MB > 129 MB L2, no flush" % (N * (6 * Q_OF[lat] * STORE_BYTES[prec] + 3 * HELD_BYTES[prec]) / 1e6),
                    "parallelism": "replicas x%d" % world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(), "kernel": "k_step<D2Q9,float,float>",

@@ -271,7 +271,7 @@ static int ensure_stage(lbm_ctx *c, size_t bytes) {
 static void default_tile(lbm_ctx *c) {
   const lbm_params &p = c->p;
   if (c->D == 1) { c->T[0] = 128; c->T[1] = 1; c->T[2] = 1; }
-  else if (c->D == 2) { c->T[0] = 64; c->T[1] = 4; c->T[2] = 1; }
+  else if (c->D == 2) { c->T[0] = 64; c->T[1] = 2; c->T[2] = 1; }
   else { c->T[0] = 32; c->T[1] = 4; c->T[2] = 2; }
   const int ga = p.g_axis;
   const int io = (p.bc_lo[ga] == LBM_BC_INLET) || (p.bc_hi[ga] == LBM_BC_OUTLET);
