@@ -180,6 +180,41 @@ const char *lbm_last_error(const lbm_ctx *c);
 /* Free the context and its device memory (synchronises); NULL-safe. */
 int lbm_destroy(lbm_ctx *c);
 
+/* ---- Diagnostics that allocate nothing ------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that may not call cudaMalloc themselves or have the library do it: an
+ * application that hands out device memory only from its own pool, or code
+ * that runs where the CUDA allocator must not be touched.
+ *
+ * It computes the same eight FP64 diagnostics as lbm_get_diag ([0] sum a_g,
+ * [1] sum a_l, [2] sum alpha_g^B, [3] sum (a_g + a_l - 1)^2, [4] max |u| over
+ * both phases, [5] nodes with a non-finite population, [6] sum (eps_g - 1),
+ * [7] sum (eps_l - 1)) of a population set the caller owns: `pops` is a
+ * device pointer to 6*Q*n_nodes doubles, full values f (not deviations),
+ * pops[(s*Q + q)*n_nodes + i] for scheme s (g, l, alpha_g, alpha_l, beta_g,
+ * beta_l), velocity q in lbm_lattice() order -- e.g. six lbm_get_populations
+ * calls with on_device = 1 into one buffer.  `spalding_mode` as in
+ * lbm_params.  `out` receives 8 doubles: a device pointer if out_on_device,
+ * else host memory (the call then synchronises `stream`).  Work is enqueued
+ * on `stream` (a cudaStream_t of the current device; NULL = legacy default).
+ *
+ * No cudaMalloc, cudaFree or other allocation happens: the per-block partial
+ * sums use one fixed scratch array of 65,600 bytes (1024 blocks x 8 doubles
+ * plus 8 results) that is a file-scope __device__ variable, so every GPU that
+ * loads the library holds it until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call uses the same array, which keeps the last call's contents (each
+ * call overwrites the parts it reads), so calls that overlap on the GPU --
+ * on different streams, or from different host threads -- race and must be
+ * serialised by the caller.
+ *
+ * Returns LBM_EINVAL for a bad lattice or Spalding mode, a NULL pointer, or
+ * n_nodes outside [1, LBM_NOALLOC_MAX_NODES]; LBM_ECUDA if a CUDA call fails. */
+#define LBM_NOALLOC_MAX_NODES 2147483647LL
+int lbm_diag_populations_noalloc(int lattice, int spalding_mode, const double *pops, long long n_nodes,
+                                 double *out, int out_on_device, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

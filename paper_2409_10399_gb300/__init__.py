@@ -82,6 +82,7 @@ def load_library(build_if_missing=True):
             "lbm_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_last_error": (ctypes.c_char_p, [P]),
             "lbm_destroy": (I, [P]),
+            "lbm_diag_populations_noalloc": (I, [I, I, dp, ctypes.c_longlong, dp, I, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -127,6 +128,18 @@ def make_params(d):
         else:
             setattr(p, k, float(v))
     return p
+
+
+def diag_populations_noalloc(lattice, spalding_mode, pops_ptr, n_nodes, out_ptr, out_on_device, stream=0):
+    """Diagnostics of a caller-owned FP64 population buffer (device pointer
+    `pops_ptr`, 6*Q*n_nodes doubles) into `out_ptr` (8 doubles) without any
+    allocation; see lbm_diag_populations_noalloc in include/lbm.h."""
+    lib = load_library()
+    rc = lib.lbm_diag_populations_noalloc(LATTICE[lattice], int(spalding_mode), ctypes.c_void_p(pops_ptr),
+                                          int(n_nodes), ctypes.c_void_p(out_ptr), int(out_on_device),
+                                          ctypes.c_void_p(int(stream or 0)))
+    if rc:
+        raise LBMError(rc, "lbm_diag_populations_noalloc")
 
 
 def _is_torch(x):
