@@ -159,7 +159,8 @@ int lbm_get_diag(lbm_ctx *c, double out[8]);
 int lbm_set_stream(lbm_ctx *c, void *cuda_stream);
 
 /* Thread-block tile of the fused step kernel, tx*ty*tz threads over
- * (x, y, z), tx*ty*tz <= 256 and a multiple of 32.  The default is chosen at
+ * (x, y, z), a multiple of 32 and at most 128 (D1Q3, D2Q9 in FP32/FP16DEV)
+ * or 256 (the other lattices and precisions).  The default is chosen at
  * lbm_create; an autotuner may try others.  With an inlet or outlet face the
  * tile along g_axis must be >= 2 (LBM_EINVAL otherwise).  Takes effect at the
  * next lbm_step; results do not depend on the tile. */

@@ -548,11 +548,20 @@ int lbm_get_diag(lbm_ctx *c, double out[8]) {
   return LBM_OK;
 }
 
+// Largest block the fused step of this lattice/precision was compiled for
+// (StepBounds in lbm_kernels.cuh).
+static int max_tile_threads(const lbm_ctx *c) {
+  if ((c->prec == LBM_FP32 || c->prec == LBM_FP16DEV) && c->D <= 2) return 128;
+  return 256;
+}
+
 int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz) {
   if (!c) return LBM_EINVAL;
   const int n = tx * ty * tz;
-  if (tx < 1 || ty < 1 || tz < 1 || n > 256 || n % 32 != 0 || (c->D < 2 && ty != 1) || (c->D < 3 && tz != 1))
-    return set_err(c, LBM_EINVAL, "invalid tile %dx%dx%d", tx, ty, tz);
+  if (tx < 1 || ty < 1 || tz < 1 || n > max_tile_threads(c) || n % 32 != 0 || (c->D < 2 && ty != 1) ||
+      (c->D < 3 && tz != 1))
+    return set_err(c, LBM_EINVAL, "invalid tile %dx%dx%d (at most %d threads, a multiple of 32)", tx, ty, tz,
+                   max_tile_threads(c));
   int old[3] = {c->T[0], c->T[1], c->T[2]};
   c->T[0] = tx;
   c->T[1] = ty;
