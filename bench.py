@@ -141,6 +141,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(x, dist=None, device="cpu"):
+    """Max of a per-rank float over all ranks (the replica timing rule)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank, steps, world, t_max):
+    """Whole-job throughput: every rank advances its own replica of
+    `nodes_per_rank` nodes for `steps` steps; the job takes the slowest rank's
+    time."""
+    return world * nodes_per_rank * steps / t_max / 1e6
+
+
+def replica_seed(base, rank):
+    """Each rank's replica starts from its own seeded fields."""
+    return base + rank
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: a
     512 x 64 strip of the box (same physics, inlet strip, walls), all host
@@ -221,7 +243,7 @@ def run_native(args, rank, world, local_rank):
     lat, dims, prec = w["lattice"], w["dims"], w["precision"]
     N = int(np.prod(dims))
     p = lparams.lattice_params(w["physics"], precision=prec, diag_every=DIAG_EVERY)
-    fields = lbm_inputs.fields_for(WORKLOAD, seed=2 + rank)
+    fields = lbm_inputs.fields_for(WORKLOAD, seed=replica_seed(2, rank))
     stream = torch.cuda.current_stream()
     sim = lbm.Simulation(lat, dims, p)
     sim.set_stream(stream)
@@ -265,10 +287,7 @@ def run_native(args, rank, world, local_rank):
     step_times = [ev[2 * j].elapsed_time(ev[2 * j + 1]) / 1e3 for j in range((K + SAMPLE - 1) // SAMPLE)
                   if (t0 + j * SAMPLE + 1) % DIAG_EVERY != 0]
     kern_s = sum(step_times) / len(step_times)
-    if dist:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = reduce_max(t_total, dist, "cuda")
     diag = sim.diag()
     if diag[5] != 0:
         raise RuntimeError("non-finite populations after the timed run")
@@ -289,16 +308,13 @@ def run_native(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     t_e2e = e0.elapsed_time(e1) / 1e3
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = reduce_max(t_e2e, dist, "cuda")
     h2d = sum(v.nbytes for v in hf.values())
     d2h = sum(v.nbytes for v in hout.values())
 
     if rank != 0:
         return
-    value = world * N * K / t_total / 1e6
+    value = aggregate_mlups(N, K, world, t_total)
     bpn = bytes_per_node(lat, prec)
     achieved = N * bpn / kern_s / 1e9
     peak, peak_kind = measured_peak()
@@ -313,7 +329,7 @@ def run_native(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(), "kernel": "k_step<D2Q9,float,float>",
                      "bytes_per_node": bpn, "kernel_ms": kern_s * 1e3, "peak_source": peak_kind},
-        "e2e": {"value": world * N * K / t_e2e / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
+        "e2e": {"value": aggregate_mlups(N, K, world, t_e2e), "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
         "gpu_launches": launches,
         "clocks": clk,
