@@ -181,6 +181,42 @@ const char *lbm_last_error(const lbm_ctx *c);
 /* Free the context and its device memory (synchronises); NULL-safe. */
 int lbm_destroy(lbm_ctx *c);
 
+/* ---- Batched form ---------------------------------------------------------
+ * Many independent lattices ("instances") of one lattice type and precision,
+ * each with its own sizes and lbm_params (density ratio, drag, ...), advanced
+ * together: one kernel launch per step over a device work list of
+ * (instance, tile) items, in lockstep (common t).  Parity and the lag latch
+ * repeat with period lcm(2, n_gamma), so when enabled (default) the launches
+ * of one period are captured once into a CUDA graph and replayed.  Every
+ * instance must use the same precision (not LBM_FP64) and n_gamma and have
+ * no inlet/outlet face (their values depend on t); LBM_EINVAL otherwise.
+ * Instance i behaves exactly like a single lbm_ctx with the same arguments.
+ * dims: 3 ints per instance (nx, ny, nz).  All other conventions as above. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(int lattice, int n, const int *dims, const lbm_params *params, lbm_batch **out);
+int lbm_batch_size(const lbm_batch *b, int *n);
+/* lbm_init of instance i; resets the common t to 0 for all instances. */
+int lbm_batch_init(lbm_batch *b, int i, const double *alpha_g, const double *u_g, const double *u_l,
+                   const double *p_k, int on_device);
+/* Enqueue n steps of every instance. */
+int lbm_batch_step(lbm_batch *b, int n);
+int lbm_batch_get_moments(lbm_batch *b, int i, double *alpha_g, double *u_g, double *u_l, double *p_k,
+                          double *S_g, double *S_l, int on_device);
+int lbm_batch_get_diag(lbm_batch *b, int i, double out[8]);
+/* Tile (work-item shape) of the batched kernel; same limits as lbm_set_tile. */
+int lbm_batch_set_tile(lbm_batch *b, int tx, int ty, int tz);
+int lbm_batch_get_tile(const lbm_batch *b, int tile[3]);
+/* Replay the steps through a captured CUDA graph (1, default) or launch them
+ * one by one (0). */
+int lbm_batch_set_graph(lbm_batch *b, int enable);
+/* Stream for all work (NULL: an internal blocking stream, ordered with the
+ * legacy default stream). */
+int lbm_batch_set_stream(lbm_batch *b, void *cuda_stream);
+int lbm_batch_time(const lbm_batch *b, long long *t);
+int lbm_batch_launch_count(const lbm_batch *b, long long *n);
+const char *lbm_batch_last_error(const lbm_batch *b);
+int lbm_batch_destroy(lbm_batch *b);
+
 /* ---- Diagnostics that allocate nothing ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that may not call cudaMalloc themselves or have the library do it: an

@@ -48,6 +48,8 @@ WORKLOADS = {
                      inlet_lo=192, inlet_hi=320, in_alpha=(0.01, 0.3), in_ug=(4.3e-4, 4.3e-3),
                      in_ul=(0.0, 0.0), inlet_ul_mode=1, ramp_nt=1667),
     ),
+    # batched sweep: 256 independent D2Q9 columns (see batch_sweep), FP32
+    "batch256": dict(lattice="D2Q9", dims=None, steps=10000, precision="fp32", physics=None),
     # 3D column, D3Q19, walls on the four x/y faces, periodic z, gravity along z.
     "column3d": dict(
         lattice="D3Q19", dims=(256, 256, 512), steps=5000, precision="fp16dev",
@@ -55,6 +57,35 @@ WORKLOADS = {
                      bc_lo=(WALL, WALL, PERIODIC), bc_hi=(WALL, WALL, PERIODIC)),
     ),
 }
+
+
+def batch_sweep(n=256, seed=4, side=(64, 512), R=(10.0, 1000.0), d_mm=(0.5, 5.0)):
+    """Parameter sweep of independent 2D D2Q9 columns (batched workload): side
+    nx uniform in `side`, ny = 4 nx, density ratio log-uniform in `R`,
+    dispersed diameter uniform in `d_mm` (mm), (R-1) g_hat = 1e-6, gamma = 1,
+    n_gamma = 200, periodic x, walls y, gravity along y, FP32.  Returns a
+    list of (dims, physics) with physics in the form of the other workloads."""
+    r = rng(seed)
+    out = []
+    for i in range(n):
+        nx = int(r.integers(side[0], side[1] + 1))
+        Ri = float(np.exp(r.uniform(np.log(R[0]), np.log(R[1]))))
+        d = float(r.uniform(d_mm[0], d_mm[1])) * 1e-3
+        ph = dict(_common_physics(Ri), d_m=d, wall_friction=False, g_axis=1,
+                  bc_lo=(PERIODIC, WALL, 0), bc_hi=(PERIODIC, WALL, 0))
+        out.append(((nx, 4 * nx, 1), ph))
+    return out
+
+
+def fields_step_profile(nx, ny, seed, low=0.9, high=0.1, noise=1e-3):
+    """alpha_g = `low` below mid-height, `high` above, plus U(-noise, noise);
+    at rest; p_k at the reference value."""
+    r = rng(seed)
+    n = nx * ny
+    y = np.arange(n) // nx
+    a = np.where(y < ny // 2, low, high) + r.uniform(-noise, noise, n)
+    z = np.zeros((2, n))
+    return dict(alpha_g=np.clip(a, 0.01, 0.99), u_g=z.copy(), u_l=z.copy(), p_k=np.full(n, CS2_PK))
 
 
 def rng(seed):

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Simulation", "LBMError", "load_library", "lattice_tables", "PRECISION", "LATTICE", "BC"]
+__all__ = ["Simulation", "Batch", "LBMError", "load_library", "lattice_tables", "PRECISION", "LATTICE", "BC"]
 
 LATTICE = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "fp64dev": 3}
@@ -83,6 +83,20 @@ def load_library(build_if_missing=True):
             "lbm_last_error": (ctypes.c_char_p, [P]),
             "lbm_destroy": (I, [P]),
             "lbm_diag_populations_noalloc": (I, [I, I, dp, ctypes.c_longlong, dp, I, P]),
+            "lbm_batch_create": (I, [I, I, ctypes.POINTER(I), ctypes.POINTER(Params), ctypes.POINTER(P)]),
+            "lbm_batch_size": (I, [P, ctypes.POINTER(I)]),
+            "lbm_batch_init": (I, [P, I, dp, dp, dp, dp, I]),
+            "lbm_batch_step": (I, [P, I]),
+            "lbm_batch_get_moments": (I, [P, I, dp, dp, dp, dp, dp, dp, I]),
+            "lbm_batch_get_diag": (I, [P, I, ctypes.POINTER(D)]),
+            "lbm_batch_set_tile": (I, [P, I, I, I]),
+            "lbm_batch_get_tile": (I, [P, ctypes.POINTER(I)]),
+            "lbm_batch_set_graph": (I, [P, I]),
+            "lbm_batch_set_stream": (I, [P, P]),
+            "lbm_batch_time": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_batch_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_batch_last_error": (ctypes.c_char_p, [P]),
+            "lbm_batch_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -128,6 +142,99 @@ def make_params(d):
         else:
             setattr(p, k, float(v))
     return p
+
+
+class Batch:
+    """Many independent lattices of one type and precision advanced together
+    (include/lbm.h, batched form).  ``Batch("D2Q9", [(nx, ny), ...],
+    [params, ...])``; instance i is initialised with ``init(i, ...)``."""
+
+    def __init__(self, lattice, dims_list, params_list):
+        self._lib = load_library()
+        self.lattice = lattice
+        self.D = LATTICE[lattice]
+        self.dims = [tuple(int(d) for d in dims) + (1,) * (3 - len(dims)) for dims in dims_list]
+        n = len(self.dims)
+        flat = (ctypes.c_int * (3 * n))(*[v for d in self.dims for v in d])
+        self._params = (Params * n)(*[make_params(p) for p in params_list])
+        h = ctypes.c_void_p()
+        rc = self._lib.lbm_batch_create(self.D, n, flat, self._params, ctypes.byref(h))
+        if rc:
+            raise LBMError(rc, "lbm_batch_create")
+        self._h = h
+        self.n = n
+        self._keep = {}
+
+    def _check(self, rc, what):
+        if rc:
+            msg = self._lib.lbm_batch_last_error(self._h)
+            raise LBMError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, i, alpha_g, u_g, u_l, p_k):
+        N = int(np.prod(self.dims[i]))
+        arrs = [np.ascontiguousarray(np.asarray(a, np.float64)) for a in (alpha_g, u_g, u_l, p_k)]
+        for a, m in zip(arrs, (N, self.D * N, self.D * N, N)):
+            if a.size != m:
+                raise ValueError("field size %d, expected %d" % (a.size, m))
+        self._check(self._lib.lbm_batch_init(self._h, int(i), *[ctypes.c_void_p(a.ctypes.data) for a in arrs], 0),
+                    "lbm_batch_init")
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def set_tile(self, tx, ty=1, tz=1):
+        self._check(self._lib.lbm_batch_set_tile(self._h, int(tx), int(ty), int(tz)), "lbm_batch_set_tile")
+
+    @property
+    def tile(self):
+        t = (ctypes.c_int * 3)()
+        self._check(self._lib.lbm_batch_get_tile(self._h, t), "lbm_batch_get_tile")
+        return tuple(t)
+
+    def set_graph(self, enable):
+        self._check(self._lib.lbm_batch_set_graph(self._h, int(bool(enable))), "lbm_batch_set_graph")
+
+    def set_stream(self, stream):
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self._stream = stream
+        self._check(self._lib.lbm_batch_set_stream(self._h, ctypes.c_void_p(handle)), "lbm_batch_set_stream")
+
+    @property
+    def t(self):
+        v = ctypes.c_longlong()
+        self._check(self._lib.lbm_batch_time(self._h, ctypes.byref(v)), "lbm_batch_time")
+        return v.value
+
+    @property
+    def launches(self):
+        v = ctypes.c_longlong()
+        self._check(self._lib.lbm_batch_launch_count(self._h, ctypes.byref(v)), "lbm_batch_launch_count")
+        return v.value
+
+    def moments(self, i):
+        N = int(np.prod(self.dims[i]))
+        D = self.D
+        res = dict(alpha_g=np.empty(N), u_g=np.empty((D, N)), u_l=np.empty((D, N)), p_k=np.empty(N),
+                   S_g=np.empty(N), S_l=np.empty(N))
+        ptrs = [ctypes.c_void_p(res[k].ctypes.data) for k in ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l")]
+        self._check(self._lib.lbm_batch_get_moments(self._h, int(i), *ptrs, 0), "lbm_batch_get_moments")
+        return res
+
+    def diag(self, i):
+        out = (ctypes.c_double * 8)()
+        self._check(self._lib.lbm_batch_get_diag(self._h, int(i), out), "lbm_batch_get_diag")
+        return np.array(out[:])
 
 
 def diag_populations_noalloc(lattice, spalding_mode, pops_ptr, n_nodes, out_ptr, out_on_device, stream=0):

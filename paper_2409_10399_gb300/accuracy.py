@@ -46,22 +46,26 @@ def _run(lattice, dims, p, fields, steps, chunk=1000):
     return m, ms / max(steps, 1), d
 
 
-def study(name, steps=None, dims=None, forms=("fp32", "fp16dev")):
+def study(name, steps=None, dims=None, forms=("fp32", "fp16dev"), spalding=None):
     w = lbm_inputs.WORKLOADS[name]
     dims = dims or w["dims"]
     steps = steps or w["steps"]
     f = lbm_inputs.fields_for(name, dims=dims)
     N = int(np.prod(dims))
     base = lparams.lattice_params(w["physics"])
+    if spalding is not None:
+        base["spalding_mode"] = spalding
     out = []
     ref, ms_ref, d_ref = _run(w["lattice"], dims, dict(base, precision="fp64"), f, steps)
-    out.append(dict(study=name, dims=list(dims), steps=steps, form="fp64", us_per_step=ms_ref * 1e3,
+    out.append(dict(study=name, dims=list(dims), steps=steps, form="fp64", spalding=base["spalding_mode"],
+                    us_per_step=ms_ref * 1e3,
                     MLUPS=N / ms_ref / 1e3, nonfinite=int(d_ref[5])))
     u_ref = np.concatenate([ref["u_g"].ravel(), ref["u_l"].ravel()])
     for form in forms:
         got, ms, d = _run(w["lattice"], dims, dict(base, precision=form), f, steps)
         u = np.concatenate([got["u_g"].ravel(), got["u_l"].ravel()])
-        out.append(dict(study=name, dims=list(dims), steps=steps, form=form, us_per_step=ms * 1e3,
+        out.append(dict(study=name, dims=list(dims), steps=steps, form=form, spalding=base["spalding_mode"],
+                        us_per_step=ms * 1e3,
                         MLUPS=N / ms / 1e3, speedup_vs_fp64=ms_ref / ms,
                         err_alpha=_rel(got["alpha_g"], ref["alpha_g"]), err_u=_rel(u, u_ref),
                         err_u_g=_rel(got["u_g"], ref["u_g"]), err_u_l=_rel(got["u_l"], ref["u_l"]),
@@ -106,8 +110,11 @@ def throughput(name, form, steps=200, dims=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--study", default="all")
+    ap.add_argument("--spalding", type=int, default=None, help="override the Spalding mode of the workloads")
     args = ap.parse_args()
     todo = []
+    if args.study == "spalding":
+        todo.append(lambda: [r for m in (0, 1, 2) for r in study("box2d", steps=5000, forms=("fp32",), spalding=m)])
     if args.study in ("box2d", "all"):
         todo.append(lambda: study("box2d"))
     if args.study in ("column3d", "all"):

@@ -31,6 +31,9 @@ cudaError_t launch_init_2(int, const MomArgs &, const double *, const double *, 
                           unsigned, cudaStream_t);
 cudaError_t launch_init_3(int, const MomArgs &, const double *, const double *, const double *, const double *,
                           unsigned, cudaStream_t);
+cudaError_t launch_batch_step_1(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
+cudaError_t launch_batch_step_2(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
+cudaError_t launch_batch_step_3(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
 cudaError_t launch_ref_step_1(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
 cudaError_t launch_ref_step_2(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
 cudaError_t launch_ref_step_3(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
@@ -64,29 +67,7 @@ __global__ void k_diag_final(const double *partials, int nblocks, double *out) {
 
 using namespace lbm;
 
-struct lbm_ctx {
-  int lattice, D, Q, prec;
-  int n[3];
-  long long N, plane;
-  lbm_params p;
-  void *pop = nullptr, *held = nullptr;
-  double *partials = nullptr, *diag_dev = nullptr;
-  double *h_diag = nullptr;  // pinned, 8 doubles
-  cudaEvent_t diag_ev = nullptr;
-  int diag_pending = 0;
-  unsigned nblk_flat = 0;
-  void *stage = nullptr;
-  size_t stage_bytes = 0;
-  cudaStream_t stream = 0;
-  long long t = 0;
-  int initialised = 0, sticky = 0;
-  double r_ag = 0.5, r_al = 0.5;
-  double mass0 = 0.0;
-  int T[3] = {1, 1, 1}, shift[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
-  size_t smem = 0;
-  long long launches = 0;
-  char err[512] = {0};
-};
+#include "lbm_internal.h"
 
 static int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
   if (c) {
@@ -270,7 +251,7 @@ static int ensure_stage(lbm_ctx *c, size_t bytes) {
 // neighbour share a block (their values are exchanged in shared memory).
 static void default_tile(lbm_ctx *c) {
   const lbm_params &p = c->p;
-  if (c->D == 1) { c->T[0] = 128; c->T[1] = 1; c->T[2] = 1; }
+  if (c->D == 1) { c->T[0] = 32; c->T[1] = 1; c->T[2] = 1; }  // small 1D domains: spread over SMs
   else if (c->D == 2) { c->T[0] = 64; c->T[1] = 2; c->T[2] = 1; }
   else { c->T[0] = 32; c->T[1] = 4; c->T[2] = 2; }
   const int ga = p.g_axis;
@@ -302,6 +283,16 @@ static int choose_tiles(lbm_ctx *c) {
   for (int d = 0; d < 3; d++) c->grid[d] = (c->n[d] + c->shift[d] + c->T[d] - 1) / c->T[d];
   return LBM_OK;
 }
+
+namespace lbm {
+StepArgs ctx_step_args(const lbm_ctx *c, long long t) { return make_args(c, t); }
+cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const WorkItem *work, unsigned nwork,
+                              dim3 block, int parity, int latch, cudaStream_t st) {
+  if (lattice == 1) return launch_batch_step_1(prec, args, work, nwork, block, parity, latch, st);
+  if (lattice == 2) return launch_batch_step_2(prec, args, work, nwork, block, parity, latch, st);
+  return launch_batch_step_3(prec, args, work, nwork, block, parity, latch, st);
+}
+}  // namespace lbm
 
 extern "C" {
 

@@ -176,8 +176,8 @@ __device__ __forceinline__ int face_rule(const StepArgs &a, const Geo &g, int q)
 
 // Slot of the read of direction q (AA rule, see the file comment).
 template <class L>
-__device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, int q, int &plane_q) {
-  if (a.parity == 0) {
+__device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, int q, int parity, int &plane_q) {
+  if (parity == 0) {
     plane_q = q;
     return g.node;
   }
@@ -191,8 +191,9 @@ __device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, 
 
 // Slot of the write of the post-collision population of direction q.
 template <class L>
-__device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g, int q, bool cross, int &plane_q) {
-  if (a.parity == 0 || cross) {
+__device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g, int q, bool cross, int parity,
+                                                int &plane_q) {
+  if (parity == 0 || cross) {
     plane_q = L::opp(q);
     return g.node;
   }
@@ -202,12 +203,12 @@ __device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g,
 
 // Load all populations of the node (deviations) with the AA read rule.
 template <class L, class S, class R>
-__device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, R f[6][L::Q]) {
+__device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, R f[6][L::Q]) {
   const S *base = (const S *)a.pop;
 #pragma unroll
   for (int q = 0; q < L::Q; q++) {
     int pq;
-    long long idx = read_slot<L>(a, g, q, pq);
+    long long idx = read_slot<L>(a, g, q, parity, pq);
 #pragma unroll
     for (int s = 0; s < 6; s++) f[s][q] = Store<S>::template ld<R>(base + (long long)(s * L::Q + pq) * a.plane + idx);
   }
@@ -321,34 +322,23 @@ template <> struct StepBounds<Lattice<2>, __half> { static constexpr int threads
 template <> struct StepBounds<Lattice<1>, float> { static constexpr int threads = 128, blocks = 4; };
 template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads = 128, blocks = 4; };
 
+// One node of the fused step (rows a1-a10).  `a` may live in kernel
+// parameter space (single lattice) or in global memory (batched instances);
+// parity and latch are the step's (t & 1, t % n_gamma == 0).  With
+// blk_xch the block exchanges the edge rows' values for the inlet/outlet
+// rules through `xch` and synchronises once, so every thread of the block
+// must call this function.
 template <class L, class S, class R>
-__global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::blocks) k_step(const StepArgs a) {
+__device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
+                                                int latch, bool blk_xch, int gstride, R *xch) {
   constexpr int D = L::D, Q = L::Q;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *xch = reinterpret_cast<R *>(smem_raw);
-
-  Geo g;
-  g.c[0] = blockIdx.x * a.T[0] + threadIdx.x - a.shift[0];
-  g.c[1] = blockIdx.y * a.T[1] + threadIdx.y - a.shift[1];
-  g.c[2] = blockIdx.z * a.T[2] + threadIdx.z - a.shift[2];
-  const bool active = g.c[0] >= 0 && g.c[0] < a.n[0] && g.c[1] >= 0 && g.c[1] < a.n[1] && g.c[2] >= 0 &&
-                      g.c[2] < a.n[2];
-  const int tid = threadIdx.x + a.T[0] * (threadIdx.y + a.T[1] * threadIdx.z);
   const int gax = a.g_axis;
-  const int gstride = gax == 0 ? 1 : (gax == 1 ? a.T[0] : a.T[0] * a.T[1]);
-  // does this block hold an inlet/outlet edge row (block-uniform)?
-  const int Tg = gax == 0 ? a.T[0] : (gax == 1 ? a.T[1] : a.T[2]);
-  const int ng = gax == 0 ? a.n[0] : (gax == 1 ? a.n[1] : a.n[2]);
-  const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
-  const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
-  const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
-
   R f[6][Q];
   Moments<L, R> m;
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
   if (active) {
     make_geo(a, D, g);
-    load_node<L, S, R>(a, g, f);
+    load_node<L, S, R>(a, g, parity, f);
     moments<L, R>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -386,7 +376,7 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
   H *held = (H *)a.held;
   R Spp_g, Spp_l, Lam;
-  if (a.latch) {
+  if (latch) {
     Spp_g = m.Sg - P.gamma * ug2 * m.deg;
     Spp_l = m.Sl - P.gamma * ul2 * dPl;
     Lam = m.alg * m.all * (m.alg + m.all * R_);  // Eq. (Lambda)
@@ -559,10 +549,67 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
       // BC_WALL: half-way bounce-back keeps out[] as is
     }
     int pq;
-    const long long idx = write_slot<L>(a, g, q, cross, pq);
+    const long long idx = write_slot<L>(a, g, q, cross, parity, pq);
 #pragma unroll
     for (int s = 0; s < 6; s++) Store<S>::template st<R>(base + (long long)(s * Q + pq) * a.plane + idx, out[s]);
   }
+}
+
+template <class L, class S, class R>
+__global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::blocks) k_step(const StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *xch = reinterpret_cast<R *>(smem_raw);
+  Geo g;
+  g.c[0] = blockIdx.x * a.T[0] + threadIdx.x - a.shift[0];
+  g.c[1] = blockIdx.y * a.T[1] + threadIdx.y - a.shift[1];
+  g.c[2] = blockIdx.z * a.T[2] + threadIdx.z - a.shift[2];
+  const bool active = g.c[0] >= 0 && g.c[0] < a.n[0] && g.c[1] >= 0 && g.c[1] < a.n[1] && g.c[2] >= 0 &&
+                      g.c[2] < a.n[2];
+  const int tid = threadIdx.x + a.T[0] * (threadIdx.y + a.T[1] * threadIdx.z);
+  const int gax = a.g_axis;
+  const int gstride = gax == 0 ? 1 : (gax == 1 ? a.T[0] : a.T[0] * a.T[1]);
+  // does this block hold an inlet/outlet edge row (block-uniform)?
+  const int Tg = gax == 0 ? a.T[0] : (gax == 1 ? a.T[1] : a.T[2]);
+  const int ng = gax == 0 ? a.n[0] : (gax == 1 ? a.n[1] : a.n[2]);
+  const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
+  const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
+  const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
+  fused_step_node<L, S, R>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
+}
+
+// Batched form: one launch advances many independent lattices (instances) of
+// the same lattice and precision.  Block b processes the tile work[b] of
+// instance work[b].inst with that instance's arguments args[inst] (global
+// memory, block-uniform); all instances share the step's parity and latch.
+// Instances have no inlet/outlet faces, so no shared-memory exchange.
+struct WorkItem {
+  int inst, x0, y0, z0;
+};
+
+// Launch bounds of the batched kernel (its constants come from shared memory).
+template <class L, class S> struct BatchBounds {
+  static constexpr int threads = StepBounds<L, S>::threads;
+  static constexpr int blocks = StepBounds<L, S>::blocks;
+};
+
+template <class L, class S, class R>
+__global__ void __launch_bounds__(BatchBounds<L, S>::threads, BatchBounds<L, S>::blocks)
+    k_batch_step(const StepArgs *__restrict__ args, const WorkItem *__restrict__ work, int parity, int latch) {
+  // the instance's constants, staged once per block in shared memory
+  __shared__ __align__(16) int sargs[(sizeof(StepArgs) + 3) / 4];
+  const WorkItem wi = work[blockIdx.x];
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int *src = reinterpret_cast<const int *>(args + wi.inst);
+  for (int k = tid; k < (int)(sizeof(StepArgs) / 4); k += nthr) sargs[k] = __ldg(src + k);
+  __syncthreads();
+  const StepArgs &a = *reinterpret_cast<const StepArgs *>(sargs);
+  Geo g;
+  g.c[0] = wi.x0 + threadIdx.x;
+  g.c[1] = wi.y0 + threadIdx.y;
+  g.c[2] = wi.z0 + threadIdx.z;
+  const bool active = g.c[0] < a.n[0] && g.c[1] < a.n[1] && g.c[2] < a.n[2];
+  fused_step_node<L, S, R>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
 }
 
 // --------------------------------------------------- moments / diagnostics
@@ -625,7 +672,7 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
     g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
     make_geo(a, D, g);
     R f[6][Q];
-    load_node<L, S, R>(a, g, f);
+    load_node<L, S, R>(a, g, a.parity, f);
     Moments<L, R> m;
     moments<L, R>(a, f, m);
     if (mode & 1) {
@@ -686,7 +733,7 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     int pq;
-    long long idx = read_slot<L>(a, g, q, pq);
+    long long idx = read_slot<L>(a, g, q, a.parity, pq);
     double dv = Store<S>::template ld<double>(base + (long long)(s * Q + pq) * a.plane + idx);
     ma.out[(long long)q * ma.N + i] = a.plain ? dv : dv + L::w(q) * r;
   }

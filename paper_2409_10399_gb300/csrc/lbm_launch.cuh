@@ -18,6 +18,13 @@ struct Launch {
     else k_step<L, __half, float><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
   }
+  static cudaError_t batch_step(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork, dim3 block,
+                                int parity, int latch, cudaStream_t st) {
+    if (prec == 3) k_batch_step<L, double, double><<<nwork, block, 0, st>>>(args, work, parity, latch);
+    else if (prec == 1) k_batch_step<L, float, float><<<nwork, block, 0, st>>>(args, work, parity, latch);
+    else k_batch_step<L, __half, float><<<nwork, block, 0, st>>>(args, work, parity, latch);
+    return cudaGetLastError();
+  }
   static cudaError_t moments(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
     if (prec == 3) k_moments<L, double, double><<<nblk, 256, 0, st>>>(ma, mode);
     else if (prec == 1) k_moments<L, float, float><<<nblk, 256, 0, st>>>(ma, mode);
@@ -52,6 +59,10 @@ cudaError_t launch_init(int lat, int prec, const MomArgs &ma, const double *a, c
   namespace lbm {                                                                                            \
   cudaError_t launch_step_##LAT(int prec, const StepArgs &a, dim3 g, dim3 b, size_t sm, cudaStream_t st) {    \
     return Launch<LAT>::step(prec, a, g, b, sm, st);                                                         \
+  }                                                                                                          \
+  cudaError_t launch_batch_step_##LAT(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork,     \
+                                     dim3 block, int parity, int latch, cudaStream_t st) {                    \
+    return Launch<LAT>::batch_step(prec, args, work, nwork, block, parity, latch, st);                        \
   }                                                                                                          \
   cudaError_t launch_moments_##LAT(int prec, const MomArgs &ma, int mode, unsigned n, cudaStream_t st) {      \
     return Launch<LAT>::moments(prec, ma, mode, n, st);                                                      \

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_step_ref(const StepArgs a) {
   double c_g[3] = {0.0, 0.0, 0.0}, c_l[3] = {0.0, 0.0, 0.0};
   if (active) {
     make_geo(a, D, g);
-    load_node<L, double, double>(a, g, f);
+    load_node<L, double, double>(a, g, a.parity, f);
     ref_moments<L>(a, f, m);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_step_ref(const StepArgs a) {
       }
     }
     int pq;
-    const long long idx = write_slot<L>(a, g, q, cross, pq);
+    const long long idx = write_slot<L>(a, g, q, cross, a.parity, pq);
 #pragma unroll
     for (int s = 0; s < 6; s++) base[(long long)(s * Q + pq) * a.plane + idx] = out[s];
   }
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(256) k_moments_ref(const MomArgs ma, int mode)
     g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
     make_geo(a, D, g);
     double f[6][Q];
-    load_node<L, double, double>(a, g, f);
+    load_node<L, double, double>(a, g, a.parity, f);
     RefMom m;
     ref_moments<L>(a, f, m);
     if (mode & 1) {

@@ -1,0 +1,94 @@
+"""Batched form: many independent lattices in one launch per step.
+
+Instance i of a batch must equal, bit for bit, a single-lattice run with the
+same sizes, parameters and fields (same per-node arithmetic); with and without
+CUDA-graph replay, for step counts that are not multiples of the graph period,
+and for every tile.  One instance is also checked against the oracle."""
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+import paper_2409_10399_gb300 as lbm
+
+pytestmark = pytest.mark.gpu
+
+PER, WALL, INLET = 0, 1, 2
+
+
+def _cases(prec="fp32"):
+    out = []
+    for i, (nx, ny, R, kap) in enumerate([(70, 37, 1000.0, 2.4e-4), (33, 60, 50.0, 1e-3), (128, 20, 10.0, 5e-3),
+                                          (64, 64, 300.0, 1e-4), (9, 11, 1000.0, 2.4e-4)]):
+        p = dict(R=R, omega_g=0.6, omega_l=120.0 / 67.0, omega_alpha=1.5, drag_model=1, kappa_I=kap,
+                 g_hat=1e-6 / (R - 1.0), g_axis=1, gamma=1.0, n_gamma=7, spalding_mode=2, precision=prec,
+                 bc_lo=(PER, WALL, 0), bc_hi=(PER, WALL, 0))
+        f = lbm_inputs.fields_random(2, (nx, ny), seed=30 + i, alpha=(0.05, 0.6), u_amp=2e-3, pk_amp=1e-5)
+        out.append(((nx, ny), p, f))
+    return out
+
+
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("steps", [1, 31])
+def test_batch_instances_equal_single_runs(graph, steps):
+    cases = _cases()
+    b = lbm.Batch("D2Q9", [c[0] for c in cases], [c[1] for c in cases])
+    b.set_graph(graph)
+    for i, c in enumerate(cases):
+        b.init(i, **c[2])
+    b.step(steps)
+    assert b.t == steps
+    for i, (dims, p, f) in enumerate(cases):
+        s = lbm.Simulation("D2Q9", dims, p)
+        s.init(**f)
+        s.step(steps)
+        got, ref = b.moments(i), s.moments()
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (i, k)
+
+
+def test_batch_tile_independent_and_graph_replays():
+    cases = _cases()
+    ref = None
+    for tile in [(64, 2, 1), (32, 4, 1), (128, 1, 1)]:
+        b = lbm.Batch("D2Q9", [c[0] for c in cases], [c[1] for c in cases])
+        b.set_tile(*tile)
+        assert b.tile == tile
+        for i, c in enumerate(cases):
+            b.init(i, **c[2])
+        b.step(14)   # one graph period (lcm(2, n_gamma = 7))
+        b.step(30)   # two replays and two direct launches
+        m = [b.moments(i) for i in range(len(cases))]
+        if ref is None:
+            ref = m
+        else:
+            for a, r in zip(m, ref):
+                for k in r:
+                    assert np.array_equal(a[k], r[k])
+
+
+def test_batch_instance_against_oracle():
+    dims, p, f = _cases()[1]
+    b = lbm.Batch("D2Q9", [dims], [p])
+    b.init(0, **f)
+    b.step(120)
+    got = b.moments(0)
+    o = oracle.Oracle("D2Q9", dims + (1,), p, threads=8)
+    o.init(**f)
+    o.step(120)
+    ref = o.moments()
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)
+    assert rel(got["alpha_g"], ref["alpha_g"]) < 1e-5
+    u = np.concatenate([got["u_g"].ravel(), got["u_l"].ravel()])
+    ur = np.concatenate([ref["u_g"].ravel(), ref["u_l"].ravel()])
+    assert rel(u, ur) < 1e-5
+
+
+def test_batch_rejects_inconsistent_instances():
+    (d0, p0, _), (d1, p1, _) = _cases()[:2]
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch("D2Q9", [d0, d1], [p0, dict(p1, n_gamma=3)])
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch("D2Q9", [d0], [dict(p0, precision="fp64")])
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch("D2Q9", [d0], [dict(p0, bc_lo=(PER, INLET, 0), inlet_lo=2, inlet_hi=6)])
