@@ -96,6 +96,17 @@ typedef struct {
                                 inside lbm_step, checked for NaN / drift */
   double drift_limit;        /* relative drift of sum(a_g) that raises
                                 LBM_EDRIFT (closed domains only); <= 0: off */
+  int beta_stencil;          /* 0: six-scheme store (6*Q population planes).
+                                1: beta-stencil form -- the beta schemes are
+                                reset to f^eq(1, c) every step (Eq. (lbmbeta)
+                                with beta = 1), so the store keeps 4*Q planes
+                                plus c_g, c_l (2*D planes, double-buffered, in
+                                the held type) and re-evaluates the streamed
+                                beta populations from c at x - v_q.  Same
+                                results (bit for bit in FP32 and FP64DEV, where
+                                c is held in the arithmetic type; FP16DEV holds
+                                c in FP32, more precise than FP16 beta planes).
+                                Not with LBM_FP64. */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
@@ -107,8 +118,9 @@ void lbm_default_params(lbm_params *p);
 
 /* Allocate a simulation of one lattice.  dim must equal the lattice's D
  * (ny = nz = 1 for D1Q3, nz = 1 for D2Q9).  Validates rates, sizes and
- * boundary codes (LBM_EINVAL), allocates 6*Q*N populations plus three held
- * fields (S''_g, S''_l, Lambda') and small scratch on the current CUDA device
+ * boundary codes (LBM_EINVAL), allocates 6*Q*N populations (4*Q*N plus
+ * 4*D*N values of c with beta_stencil) plus three held fields (S''_g,
+ * S''_l, Lambda') and small scratch on the current CUDA device
  * (LBM_ENOMEM).  *out is NULL on failure. */
 int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p, lbm_ctx **out);
 
@@ -189,8 +201,10 @@ int lbm_destroy(lbm_ctx *c);
  * repeat with period lcm(2, n_gamma), so when enabled (default) the launches
  * of one period are captured once into a CUDA graph and replayed.  Every
  * instance must use the same precision (not LBM_FP64) and n_gamma and have
- * no inlet/outlet face (their values depend on t); LBM_EINVAL otherwise.
- * Instance i behaves exactly like a single lbm_ctx with the same arguments.
+ * no inlet/outlet face (their values depend on t) and the six-scheme store
+ * (beta_stencil = 0); LBM_EINVAL otherwise.
+ * Instance i computes what a single lbm_ctx with the same arguments computes
+ * (the same node arithmetic in a second kernel; equal up to rounding).
  * dims: 3 ints per instance (nx, ny, nz).  All other conventions as above. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(int lattice, int n, const int *dims, const lbm_params *params, lbm_batch **out);

@@ -45,6 +45,7 @@ class Params(ctypes.Structure):
         ("in_alpha", ctypes.c_double * 2), ("in_ug", ctypes.c_double * 2), ("in_ul", ctypes.c_double * 2),
         ("ramp_nt", ctypes.c_int), ("inlet_ul_mode", ctypes.c_int),
         ("precision", ctypes.c_int), ("diag_every", ctypes.c_int), ("drift_limit", ctypes.c_double),
+        ("beta_stencil", ctypes.c_int),
     ]
 
 

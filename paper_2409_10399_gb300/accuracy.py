@@ -94,17 +94,17 @@ def sensitivity(name, rel_perturbation, steps=None, dims=None, seed=99):
                 err_pk=_rel(b["p_k"] - 1 / 3, a["p_k"] - 1 / 3))
 
 
-def throughput(name, form, steps=200, dims=None):
+def throughput(name, form, steps=200, dims=None, beta_stencil=0):
     """Device time per step of one form at the workload's full size."""
     w = lbm_inputs.WORKLOADS[name]
     dims = dims or w["dims"]
     f = lbm_inputs.fields_for(name, dims=dims)
     N = int(np.prod(dims))
-    p = lparams.lattice_params(w["physics"], precision=form)
+    p = dict(lparams.lattice_params(w["physics"], precision=form), beta_stencil=beta_stencil)
     _run(w["lattice"], dims, p, f, 20)
     m, ms, d = _run(w["lattice"], dims, p, f, steps)
-    return dict(study=name + "_throughput", dims=list(dims), steps=steps, form=form, us_per_step=ms * 1e3,
-                MLUPS=N / ms / 1e3, nonfinite=int(d[5]))
+    return dict(study=name + "_throughput", dims=list(dims), steps=steps, form=form, beta_stencil=beta_stencil,
+                us_per_step=ms * 1e3, MLUPS=N / ms / 1e3, nonfinite=int(d[5]))
 
 
 def main():
@@ -113,6 +113,10 @@ def main():
     ap.add_argument("--spalding", type=int, default=None, help="override the Spalding mode of the workloads")
     args = ap.parse_args()
     todo = []
+    if args.study == "bstencil":
+        todo.append(lambda: [throughput(n, f, steps=400, beta_stencil=b) for n, f in
+                             (("box2d", "fp32"), ("box2d", "fp16dev"), ("column3d", "fp16dev"), ("column3d", "fp32"))
+                             for b in (0, 1)])
     if args.study == "spalding":
         todo.append(lambda: [r for m in (0, 1, 2) for r in study("box2d", steps=5000, forms=("fp32",), spalding=m)])
     if args.study in ("box2d", "all"):

@@ -121,7 +121,7 @@ int lbm_batch_create(int lattice, int n, const int *dims, const lbm_params *para
   for (int i = 0; i < n; i++) {
     const lbm_params &p = params[i];
     if (p.precision != prec || p.n_gamma != ng || p.bc_lo[p.g_axis] == LBM_BC_INLET ||
-        p.bc_hi[p.g_axis] == LBM_BC_OUTLET) {
+        p.bc_hi[p.g_axis] == LBM_BC_OUTLET || p.beta_stencil) {
       lbm_batch_destroy(b);
       return LBM_EINVAL;
     }

@@ -202,6 +202,8 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.ugIN = ramp(p.in_ug, t, p.ramp_nt);
   a.ulIN = p.inlet_ul_mode == 1 ? -a.aIN * a.ugIN / (1.0 - a.aIN) : ramp(p.in_ul, t, p.ramp_nt);
   a.plain = c->prec == LBM_FP64;
+  a.cfield = c->cfield;
+  a.beta_own = c->cfield && t == 0;
   // the same constants in the kernels' arithmetic types
   PhysT<double> &d = a.pd;
   d.R_ = a.R; d.invR = a.invR; d.omega_g = a.omega_g; d.omega_l = a.omega_l; d.omega_a = a.omega_a;
@@ -209,6 +211,12 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   d.eta0_l = a.eta0_l; d.psi_g = a.psi_g; d.psi_l = a.psi_l; d.k0 = a.k0; d.kappa_I = a.kappa_I;
   d.kappa_W = a.kappa_W; d.buoy = a.buoy; d.gamma = a.gamma; d.afloor = a.afloor; d.r_ag = a.r_ag;
   d.r_al = a.r_al; d.aIN = a.aIN; d.ugIN = a.ugIN; d.ulIN = a.ulIN;
+  {
+    // r_ag + r_al - 1 exactly (two-sum of the double references)
+    const double sm = d.r_ag + d.r_al, bb = sm - d.r_ag;
+    const double er = (d.r_ag - (sm - bb)) + (d.r_al - bb);
+    d.rsum1 = (sm - 1.0) + er;
+  }
   PhysT<float> &f = a.pf;
   f.R_ = (float)d.R_; f.invR = (float)d.invR; f.omega_g = (float)d.omega_g; f.omega_l = (float)d.omega_l;
   f.omega_a = (float)d.omega_a; f.kgrad = (float)d.kgrad; f.A_g = (float)d.A_g; f.B_g = (float)d.B_g;
@@ -216,6 +224,8 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   f.psi_g = (float)d.psi_g; f.psi_l = (float)d.psi_l; f.k0 = (float)d.k0; f.kappa_I = (float)d.kappa_I;
   f.kappa_W = (float)d.kappa_W; f.buoy = (float)d.buoy; f.gamma = (float)d.gamma; f.afloor = (float)d.afloor;
   f.r_ag = (float)d.r_ag; f.r_al = (float)d.r_al; f.aIN = (float)d.aIN; f.ugIN = (float)d.ugIN;
+  // float references sum exactly in double
+  f.rsum1 = (float)(((double)f.r_ag + (double)f.r_al) - 1.0);
   f.ulIN = (float)d.ulIN;
   a.cs2 = CS2;
   a.two_cs4 = 2.0 * CS2 * CS2;
@@ -332,7 +342,8 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   if (!(q.R >= 1.0) || !(q.omega_g > 0 && q.omega_g < 2) || !(q.omega_l > 0 && q.omega_l < 2) ||
       !(q.omega_alpha > 0 && q.omega_alpha < 2) || q.n_gamma < 1 || q.spalding_mode < 0 || q.spalding_mode > 2 ||
       !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 3 ||
-      (q.drag_model != LBM_DRAG_CONST && q.drag_model != LBM_DRAG_CGW) || q.diag_every < 0)
+      (q.drag_model != LBM_DRAG_CONST && q.drag_model != LBM_DRAG_CGW) || q.diag_every < 0 ||
+      (q.beta_stencil != 0 && q.beta_stencil != 1) || (q.beta_stencil && q.precision == LBM_FP64))
     return LBM_EINVAL;
   int dims[3] = {nx, ny, nz};
   for (int d = 0; d < dim; d++) {
@@ -363,9 +374,12 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   default_tile(c);
   int rc = choose_tiles(c);
   if (rc) { int e = rc; delete c; return e; }
-  size_t pop_bytes = (size_t)6 * c->Q * c->plane * store_size(c->prec);
+  const int nsch = q.beta_stencil ? 4 : 6;
+  size_t pop_bytes = (size_t)nsch * c->Q * c->plane * store_size(c->prec);
   size_t held_bytes = (size_t)3 * c->plane * held_size(c->prec);
+  size_t c_bytes = (size_t)4 * dim * c->plane * held_size(c->prec);
   if (cudaMalloc(&c->pop, pop_bytes) != cudaSuccess || cudaMalloc(&c->held, held_bytes) != cudaSuccess ||
+      (q.beta_stencil && cudaMalloc(&c->cfield, c_bytes) != cudaSuccess) ||
       cudaMalloc((void **)&c->partials, (size_t)c->nblk_flat * 8 * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void **)&c->diag_dev, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void **)&c->h_diag, 8 * sizeof(double)) != cudaSuccess ||
@@ -591,6 +605,7 @@ int lbm_destroy(lbm_ctx *c) {
   if (c->stream || c->pop) cudaStreamSynchronize(c->stream);
   if (c->pop) cudaFree(c->pop);
   if (c->held) cudaFree(c->held);
+  if (c->cfield) cudaFree(c->cfield);
   if (c->partials) cudaFree(c->partials);
   if (c->diag_dev) cudaFree(c->diag_dev);
   if (c->h_diag) cudaFreeHost(c->h_diag);

@@ -12,6 +12,7 @@ struct lbm_ctx {
   long long N, plane;
   lbm_params p;
   void *pop = nullptr, *held = nullptr;
+  void *cfield = nullptr;    // beta-stencil form: 2 x 2*D planes of c
   double *partials = nullptr, *diag_dev = nullptr;
   double *h_diag = nullptr;  // pinned, 8 doubles
   cudaEvent_t diag_ev = nullptr;

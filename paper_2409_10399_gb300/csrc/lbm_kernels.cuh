@@ -17,6 +17,17 @@
 // node's own slot (x, opp q) on the write side, carrying the face rule's value
 // (half-way bounce-back, Table 1 inlet, Table 2 outlet), and is read back from
 // slot (x, q) on the odd read side.
+//
+// Beta-stencil form (template flag BS): the beta schemes are reset to
+// f^eq(1, c) at every node and step (Eq. (lbmbeta) with beta = 1), so what
+// streams into node x along q is a function of c at the source node only.
+// The store then keeps 4*Q population planes and, instead of the 2*Q beta
+// planes, the 2*D components of c (c_g, c_l) of the last step in a
+// double-buffered field (buffer t & 1 written at step t, the other read); the
+// beta populations arriving at x are re-evaluated from c at x - v_q, or from
+// the face rule at x where x - v_q lies beyond a non-periodic face.  The
+// arithmetic is the six-scheme form's, so with c held in the kernel's type
+// the two forms give the same bits.
 #pragma once
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -37,6 +48,7 @@ template <class R> struct PhysT {
   R eta0_g, eta0_l, psi_g, psi_l, k0;            // eta_q(psi) rest / moving; (1-w0)/w0
   R kappa_I, kappa_W, buoy, gamma, afloor;
   R r_ag, r_al;                                  // deviation references of f_alpha
+  R rsum1;                                       // r_ag + r_al - 1 of the references above
   R aIN, ugIN, ulIN;                             // inlet values at this t
 };
 
@@ -54,6 +66,8 @@ struct StepArgs {
   int g_axis, tr_axis;  // gravity / inlet-normal axis, first transverse axis (-1 in 1D)
   int inlet_lo, inlet_hi;
   int has_inlet, has_outlet;
+  void *cfield;         // beta-stencil form: 2 buffers x 2*D planes of c (held type)
+  int beta_own;         // beta-stencil form, first step after init: every q from the node's own c
   // physics
   double invR, R, omega_g, omega_l, omega_a, kgrad;  // kgrad = omega_alpha / cs2
   double A_g, B_g, A_l, B_l;                         // sigma = A (Pi^eq - Pi) + B S'' I
@@ -201,8 +215,109 @@ __device__ __forceinline__ long long write_slot(const StepArgs &a, const Geo &g,
   return shifted_node<L>(a, g, q, +1);
 }
 
-// Load all populations of the node (deviations) with the AA read rule.
+// v_q . u
+template <class L, class R>
+__device__ __forceinline__ R vdot(int q, const R u[3]) {
+  R s = R(0);
+#pragma unroll
+  for (int d = 0; d < L::D; d++) {
+    const int vd = L::v(q, d);
+    if (vd == 1) s += u[d];
+    if (vd == -1) s -= u[d];
+  }
+  return s;
+}
+
+template <class L, class R> __device__ __forceinline__ R feqS_dv(int q, R alpha, R alpha_dev, const R u[3], R uu);
+template <class L> __device__ __forceinline__ int face_rule(const StepArgs &a, const Geo &g, int q);
+
+// Beta-stencil form: c_g, c_l of the last step at node `node` (buffer `buf`).
 template <class L, class S, class R>
+__device__ __forceinline__ void load_c(const StepArgs &a, int buf, long long node, R cg[3], R cl[3]) {
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  const H *cb = (const H *)a.cfield + (long long)buf * 2 * L::D * a.plane;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    cg[d] = d < L::D ? (R)__ldg(cb + d * a.plane + node) : R(0);
+    cl[d] = d < L::D ? (R)__ldg(cb + (L::D + d) * a.plane + node) : R(0);
+  }
+}
+
+// Operations rounded one by one, which the compiler neither fuses nor reorders.
+template <class R> struct Rn;
+template <> struct Rn<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Rn<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+// f^eq(1, c)_q - w_q of the beta schemes (Eq. (equilibrium) with alpha = 1),
+// in explicitly rounded steps: the six-scheme store evaluates it on the write
+// side and the beta-stencil form on the read side, and both must give the
+// same bits.
+template <class L, class R>
+__device__ __forceinline__ R beta_dev(int q, const R c[3]) {
+  R c2 = R(0);
+#pragma unroll
+  for (int d = 0; d < L::D; d++) c2 = Rn<R>::fma(c[d], c[d], c2);
+  const R vc = vdot<L, R>(q, c);
+  const R t = Rn<R>::fma(Rn<R>::mul(R(4.5), vc), vc, Rn<R>::fma(R(3), vc, Rn<R>::mul(R(-1.5), c2)));
+  return Rn<R>::mul((R)L::w(q), t);
+}
+
+template <class L, class R>
+__device__ __forceinline__ void beta_pair(int q, const R cg[3], const R cl[3], R &bg, R &bl) {
+  bg = beta_dev<L, R>(q, cg);
+  bl = beta_dev<L, R>(q, cl);
+}
+
+// Beta-stencil form: the beta deviations arriving at the node along every q,
+// as the six-scheme store would hold them (the write side of the step that
+// produced c, replayed).
+template <class L, class S, class R>
+__device__ __forceinline__ void load_beta(const StepArgs &a, const Geo &g, int parity, R fbg[L::Q], R fbl[L::Q]) {
+  const int buf = 1 - parity;
+  R cg0[3], cl0[3];
+  load_c<L, S, R>(a, buf, g.node, cg0, cl0);
+#pragma unroll
+  for (int q = 0; q < L::Q; q++) {
+    const int qo = L::opp(q);
+    if (a.beta_own) {
+      beta_pair<L, R>(q, cg0, cl0, fbg[q], fbl[q]);   // initial state: f^eq(1, c(x))
+    } else if (!crosses<L>(g, q, -1)) {
+      R cg[3], cl[3];
+      load_c<L, S, R>(a, buf, shifted_node<L>(a, g, q, -1), cg, cl);
+      beta_pair<L, R>(q, cg, cl, fbg[q], fbl[q]);     // streamed from x - v_q
+    } else {
+      const int rule = face_rule<L>(a, g, qo);          // the rule that sent opp(q) back
+      if (rule == BC_INLET || rule == BC_OUTLET) {
+        // Tables 1-2: f_beta EQ(S) with c extrapolated full-way from the
+        // inward neighbour along the face normal
+        const int gax = a.g_axis;
+        int st = gax == 0 ? 1 : (gax == 1 ? a.n[0] : a.n[0] * a.n[1]);
+        if (rule == BC_OUTLET) st = -st;
+        R cgn[3], cln[3], cb[3], cc[3];
+        load_c<L, S, R>(a, buf, g.node + st, cgn, cln);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          cb[d] = R(2) * cg0[d] - cgn[d];
+          cc[d] = R(2) * cl0[d] - cln[d];
+        }
+        beta_pair<L, R>(q, cb, cc, fbg[q], fbl[q]);
+      } else {
+        beta_pair<L, R>(qo, cg0, cl0, fbg[q], fbl[q]);  // half-way bounce-back
+      }
+    }
+  }
+}
+
+// Load all populations of the node (deviations) with the AA read rule.
+template <class L, class S, class R, bool BS = false>
 __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, R f[6][L::Q]) {
   const S *base = (const S *)a.pop;
 #pragma unroll
@@ -210,8 +325,10 @@ __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int p
     int pq;
     long long idx = read_slot<L>(a, g, q, parity, pq);
 #pragma unroll
-    for (int s = 0; s < 6; s++) f[s][q] = Store<S>::template ld<R>(base + (long long)(s * L::Q + pq) * a.plane + idx);
+    for (int s = 0; s < (BS ? 4 : 6); s++)
+      f[s][q] = Store<S>::template ld<R>(base + (long long)(s * L::Q + pq) * a.plane + idx);
   }
+  if (BS) load_beta<L, S, R>(a, g, parity, f[4], f[5]);
 }
 
 // ------------------------------------------------------------- moments
@@ -221,8 +338,10 @@ template <class L, class R> struct Moments {
   R ug[3], ul[3];
   R Pg[6], Pl[6];        // Pi - cs2 I, packed xx, yy, zz, xy, xz, yz
   R ag, al, Jg[3], Jl[3];
+  R dag, dal;            // a - r (sums of the alpha deviations)
   R Sg, Sl;              // 1 - beta
   R alg, all;            // alpha^B
+  R dalg, dall;          // alpha^B - r
 };
 
 __host__ __device__ constexpr int pidx(int a, int b) {
@@ -267,43 +386,52 @@ __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], M
       }
     }
   }
+  m.dag = m.ag;
+  m.dal = m.al;
   m.ag += P.r_ag;
   m.al += P.r_al;
   if (a.spalding == 0) {
     m.alg = m.ag;
     m.all = m.al;
+    m.dalg = m.dag;
+    m.dall = m.dal;
   } else {
-    // Eq. (spalding) with B(x) = x clamped to [0, 1]
-    R Bg = m.ag < R(0) ? R(0) : (m.ag > R(1) ? R(1) : m.ag);
-    R Bl = m.al < R(0) ? R(0) : (m.al > R(1) ? R(1) : m.al);
-    R sum = Bg + Bl;
-    m.alg = sum > R(0) ? Bg / sum : R(0.5);
-    m.all = R(1) - m.alg;
+    // Eq. (spalding) with B(x) = x clamped to [0, 1].  Inside [0, 1] the
+    // normalisation is formed in deviations, alpha^B - r = (a - r) - a e/(1 + e)
+    // with e = a_g + a_l - 1 = (a_g - r_g) + (a_l - r_l) + (r_g + r_l - 1), so
+    // the small quantities keep their own precision instead of the spacing of
+    // alpha^B itself.
+    if (m.ag >= R(0) && m.ag <= R(1) && m.al >= R(0) && m.al <= R(1) && m.ag + m.al > R(0)) {
+      const R e = (m.dag + m.dal) + P.rsum1;
+      m.dalg = m.dag - m.ag * (e / (R(1) + e));
+    } else {
+      R Bg = m.ag < R(0) ? R(0) : (m.ag > R(1) ? R(1) : m.ag);
+      R Bl = m.al < R(0) ? R(0) : (m.al > R(1) ? R(1) : m.al);
+      R sum = Bg + Bl;
+      m.dalg = (sum > R(0) ? Bg / sum : R(0.5)) - P.r_ag;
+    }
+    m.dall = -m.dalg - P.rsum1;  // alpha^B_l = 1 - alpha^B_g
+    m.alg = P.r_ag + m.dalg;
+    m.all = P.r_al + m.dall;
   }
 }
 
 // ------------------------------------------------------------ fused step
 
-template <class L, class R>
-__device__ __forceinline__ R vdot(int q, const R u[3]) {
-  R s = R(0);
-#pragma unroll
-  for (int d = 0; d < L::D; d++) {
-    const int vd = L::v(q, d);
-    if (vd == 1) s += u[d];
-    if (vd == -1) s -= u[d];
-  }
-  return s;
-}
 
 // f^eq(alpha, u)_q - w_q*r with the quadratic term of Eq. (equilibrium),
 // grouped as w [(alpha - r) + alpha (3 v.u + 9/2 (v.u)^2 - 3/2 u^2)] so that
 // alpha = r (the beta schemes, r = 1) loses nothing to cancellation.
 template <class L, class R>
-__device__ __forceinline__ R feqS_dev(int q, R alpha, const R u[3], R uu, R r) {
+__device__ __forceinline__ R feqS_dv(int q, R alpha, R alpha_dev, const R u[3], R uu) {
   const R w = (R)L::w(q);
   const R vu = vdot<L, R>(q, u);
-  return w * ((alpha - r) + alpha * (R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu));
+  return w * (alpha_dev + alpha * (R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu));
+}
+// the same with alpha - r formed here
+template <class L, class R>
+__device__ __forceinline__ R feqS_dev(int q, R alpha, const R u[3], R uu, R r) {
+  return feqS_dv<L, R>(q, alpha, alpha - r, u, uu);
 }
 
 // Values a face rule streams back into the node, as deviations.  xn holds the
@@ -328,7 +456,7 @@ template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads
 // blk_xch the block exchanges the edge rows' values for the inlet/outlet
 // rules through `xch` and synchronises once, so every thread of the block
 // must call this function.
-template <class L, class S, class R>
+template <class L, class S, class R, bool BS = false>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
                                                 int latch, bool blk_xch, int gstride, R *xch) {
   constexpr int D = L::D, Q = L::Q;
@@ -338,12 +466,22 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
   if (active) {
     make_geo(a, D, g);
-    load_node<L, S, R>(a, g, parity, f);
+    load_node<L, S, R, BS>(a, g, parity, f);
     moments<L, R>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
       cg[d] = m.all * (m.ug[d] - m.ul[d]);  // Eq. (velocitybeta) with beta = 1
       cl[d] = m.alg * (m.ul[d] - m.ug[d]);
+    }
+  }
+  if (BS && active) {
+    // beta-stencil form: c of this step into buffer t & 1
+    typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+    H *cw = (H *)a.cfield + (long long)parity * 2 * D * a.plane;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      cw[d * a.plane + g.node] = (H)cg[d];
+      cw[(D + d) * a.plane + g.node] = (H)cl[d];
     }
   }
   if (blk_xch) {
@@ -460,13 +598,8 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   const R om_g = P.omega_g, om_l = P.omega_l, om_a = P.omega_a;
   const R k0 = P.k0;
   const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
+  const R deq_g = a.spalding == 2 ? m.dalg : m.dag, deq_l = a.spalding == 2 ? m.dall : m.dal;
   const R rag = P.r_ag, ral = P.r_al;
-  R c2g = R(0), c2l = R(0);
-#pragma unroll
-  for (int d = 0; d < D; d++) {
-    c2g += cg[d] * cg[d];
-    c2l += cl[d] * cl[d];
-  }
   // equilibrium offsets of f_I^eq - w: rest and moving directions, Eq. (eta)
   const R eI_g0 = m.deg, eI_gq = m.deg;                 // phi_g = 1
   const R eI_l0 = m.del + k0 * (m.del - dPl), eI_lq = dPl;
@@ -483,10 +616,9 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
              w * ((q == 0 ? eL_g0 : eL_gq) + R(3) * vGg);
     out[1] = f[1][q] + om_l * (w * ((q == 0 ? eI_l0 : eI_lq) + R(3) * vul + R(4.5) * vul * vul - R(1.5) * ul2) - f[1][q]) +
              w * ((q == 0 ? eL_l0 : eL_lq) + R(3) * vGl);
-    out[2] = f[2][q] + om_a * (feqS_dev<L, R>(q, aeq_g, m.ug, ug2, rag) - f[2][q]);
-    out[3] = f[3][q] + om_a * (feqS_dev<L, R>(q, aeq_l, m.ul, ul2, ral) - f[3][q]);
-    out[4] = feqS_dev<L, R>(q, R(1), cg, c2g, R(1));
-    out[5] = feqS_dev<L, R>(q, R(1), cl, c2l, R(1));
+    out[2] = f[2][q] + om_a * (feqS_dv<L, R>(q, aeq_g, deq_g, m.ug, ug2) - f[2][q]);
+    out[3] = f[3][q] + om_a * (feqS_dv<L, R>(q, aeq_l, deq_l, m.ul, ul2) - f[3][q]);
+    if (!BS) beta_pair<L, R>(q, cg, cl, out[4], out[5]);
 
     const bool cross = crosses<L>(g, q, +1);
     if (cross) {
@@ -507,23 +639,20 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         out[2] = feqS_dev<L, R>(qo, P.aIN, uin, P.ugIN * P.ugIN, rag);
         out[3] = feqS_dev<L, R>(qo, R(1) - P.aIN, lin, P.ulIN * P.ulIN, ral);
         const R *xn = xch + (tid + gstride) * XCH;
-        R cb[3] = {R(0), R(0), R(0)}, cc[3] = {R(0), R(0), R(0)}, cb2 = R(0), cc2 = R(0);
+        R cb[3] = {R(0), R(0), R(0)}, cc[3] = {R(0), R(0), R(0)};
 #pragma unroll
         for (int d = 0; d < D; d++) {
           cb[d] = R(2) * cg[d] - xn[8 + d];
           cc[d] = R(2) * cl[d] - xn[11 + d];
-          cb2 += cb[d] * cb[d];
-          cc2 += cc[d] * cc[d];
         }
-        out[4] = feqS_dev<L, R>(qo, R(1), cb, cb2, R(1));
-        out[5] = feqS_dev<L, R>(qo, R(1), cc, cc2, R(1));
+        if (!BS) beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
       } else if (rule == BC_OUTLET) {
         // Table 2: f_g, f_l ABB(I) with eps = 1 (so phi = 1) and u EX(hw);
         // f_alpha ABB(S) with alpha, u EX(hw); f_beta EQ(S) with c EX(fw).
         const R *xn = xch + (tid - gstride) * XCH;
         R ubg[3] = {R(0), R(0), R(0)}, ubl[3] = {R(0), R(0), R(0)}, cb[3] = {R(0), R(0), R(0)},
           cc[3] = {R(0), R(0), R(0)};
-        R ubg2 = R(0), ubl2 = R(0), cb2 = R(0), cc2 = R(0);
+        R ubg2 = R(0), ubl2 = R(0);
 #pragma unroll
         for (int d = 0; d < D; d++) {
           ubg[d] = R(1.5) * m.ug[d] - R(0.5) * xn[d];
@@ -532,8 +661,6 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
           cc[d] = R(2) * cl[d] - xn[11 + d];
           ubg2 += ubg[d] * ubg[d];
           ubl2 += ubl[d] * ubl[d];
-          cb2 += cb[d] * cb[d];
-          cc2 += cc[d] * cc[d];
         }
         const R vbg = vdot<L, R>(q, ubg), vbl = vdot<L, R>(q, ubl);
         const R qg = R(4.5) * vbg * vbg - R(1.5) * ubg2, ql = R(4.5) * vbl * vbl - R(1.5) * ubl2;
@@ -543,19 +670,19 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         const R abl = R(1.5) * m.all - R(0.5) * xn[7];
         out[2] = -out[2] + R(2) * w * ((abg - rag) + abg * qg);
         out[3] = -out[3] + R(2) * w * ((abl - ral) + abl * ql);
-        out[4] = feqS_dev<L, R>(qo, R(1), cb, cb2, R(1));
-        out[5] = feqS_dev<L, R>(qo, R(1), cc, cc2, R(1));
+        if (!BS) beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
       }
       // BC_WALL: half-way bounce-back keeps out[] as is
     }
     int pq;
     const long long idx = write_slot<L>(a, g, q, cross, parity, pq);
 #pragma unroll
-    for (int s = 0; s < 6; s++) Store<S>::template st<R>(base + (long long)(s * Q + pq) * a.plane + idx, out[s]);
+    for (int s = 0; s < (BS ? 4 : 6); s++)
+      Store<S>::template st<R>(base + (long long)(s * Q + pq) * a.plane + idx, out[s]);
   }
 }
 
-template <class L, class S, class R>
+template <class L, class S, class R, bool BS>
 __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::blocks) k_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *xch = reinterpret_cast<R *>(smem_raw);
@@ -574,14 +701,17 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
   const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
-  fused_step_node<L, S, R>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
+  fused_step_node<L, S, R, BS>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
 }
 
 // Batched form: one launch advances many independent lattices (instances) of
 // the same lattice and precision.  Block b processes the tile work[b] of
 // instance work[b].inst with that instance's arguments args[inst] (global
 // memory, block-uniform); all instances share the step's parity and latch.
-// Instances have no inlet/outlet faces, so no shared-memory exchange.
+// Instances have no inlet/outlet faces, so no shared-memory exchange.  The
+// node arithmetic is the single-lattice kernel's source, compiled into a
+// second kernel: the compiler may fuse multiply-adds differently there, so
+// the two agree to rounding, not bit for bit.
 struct WorkItem {
   int inst, x0, y0, z0;
 };
@@ -659,7 +789,7 @@ __device__ __forceinline__ void block_diag_reduce(double v[8], double *partials)
 }
 
 // One thread per node over a flat 1D grid (block 256).
-template <class L, class S, class R>
+template <class L, class S, class R, bool BS>
 __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
   constexpr int D = L::D, Q = L::Q;
   const StepArgs &a = ma.s;
@@ -672,13 +802,13 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
     g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
     make_geo(a, D, g);
     R f[6][Q];
-    load_node<L, S, R>(a, g, a.parity, f);
+    load_node<L, S, R, BS>(a, g, a.parity, f);
     Moments<L, R> m;
     moments<L, R>(a, f, m);
     if (mode & 1) {
       double *o = ma.out;
       const long long N = ma.N;
-      o[i] = (double)m.alg;
+      o[i] = (double)phys<R>(a).r_ag + (double)m.dalg;  // reference plus deviation, in FP64
       for (int d = 0; d < D; d++) {
         o[(1 + d) * N + i] = (double)m.ug[d];
         o[(1 + D + d) * N + i] = (double)m.ul[d];
@@ -698,10 +828,11 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
         ug2 += (double)m.ug[d] * (double)m.ug[d];
         ul2 += (double)m.ul[d] * (double)m.ul[d];
       }
-      double sum = (double)m.ag + (double)m.al - 1.0;
-      v[0] = m.ag;
-      v[1] = m.al;
-      v[2] = m.alg;
+      const PhysT<R> &P = phys<R>(a);
+      double sum = ((double)m.dag + (double)m.dal) + (double)P.rsum1;
+      v[0] = (double)P.r_ag + (double)m.dag;
+      v[1] = (double)P.r_al + (double)m.dal;
+      v[2] = (double)P.r_ag + (double)m.dalg;
       v[3] = sum * sum;
       v[4] = sqrt(fmax(ug2, ul2));
       v[5] = bad ? 1.0 : 0.0;
@@ -717,7 +848,7 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
 __global__ void k_diag_final(const double *partials, int nblocks, double *out);
 
 // Full populations (f, not deviations) of scheme s in [q][node] order.
-template <class L, class S, class R>
+template <class L, class S, class R, bool BS>
 __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
   constexpr int D = L::D, Q = L::Q;
   const StepArgs &a = ma.s;
@@ -729,7 +860,16 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
   g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
   make_geo(a, D, g);
   const S *base = (const S *)a.pop;
-  const double r = a.plain ? 0.0 : (s == 2 ? a.r_ag : (s == 3 ? a.r_al : 1.0));
+  // the references the step kernel adds (in its arithmetic type)
+  const double rg = sizeof(S) == 8 ? a.r_ag : (double)a.pf.r_ag, rl = sizeof(S) == 8 ? a.r_al : (double)a.pf.r_al;
+  const double r = a.plain ? 0.0 : (s == 2 ? rg : (s == 3 ? rl : 1.0));
+  if (BS && s >= 4) {
+    R fb[2][Q];
+    load_beta<L, S, R>(a, g, a.parity, fb[0], fb[1]);
+#pragma unroll
+    for (int q = 0; q < Q; q++) ma.out[(long long)q * ma.N + i] = (double)fb[s - 4][q] + L::w(q) * r;
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     int pq;
@@ -744,7 +884,7 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
 // Equilibria of every scheme from FP64 fields (Sec. 2, initial state), written
 // in the even-step layout (slot (x, q) holds f(x, q)); held S'' = 0, Lambda' =
 // Lambda(alpha_g).  Computed in double, stored in S.
-template <class L, class S>
+template <class L, class S, bool BS>
 __global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *alpha_g, const double *u_g,
                                              const double *u_l, const double *p_k) {
   constexpr int D = L::D, Q = L::Q;
@@ -760,16 +900,25 @@ __global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *al
   const double ag = alpha_g[i], al = 1.0 - ag;
   const double deg = p_k[i] * 3.0 - 1.0;  // eps_g - 1, Eq. (sigmag1D); eps_l = 1
   const double dPl = deg * a.invR;        // phi*eps_l - 1, Eq. (lbm-phi-l)
-  double ug2 = 0, ul2 = 0, cg2 = 0, cl2 = 0;
+  double ug2 = 0, ul2 = 0;
   for (int d = 0; d < D; d++) {
     cg[d] = al * (ug[d] - ul[d]);
     cl[d] = ag * (ul[d] - ug[d]);
     ug2 += ug[d] * ug[d];
     ul2 += ul[d] * ul[d];
-    cg2 += cg[d] * cg[d];
-    cl2 += cl[d] * cl[d];
   }
   S *base = (S *)a.pop;
+  // c in the step kernel's arithmetic type H, and the beta equilibria from
+  // it as that kernel evaluates them (beta_dev), so the beta-stencil form,
+  // which starts from the same c, sees the same initial beta populations
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  H cgH[3] = {H(0), H(0), H(0)}, clH[3] = {H(0), H(0), H(0)};
+  for (int d = 0; d < D; d++) {
+    cgH[d] = (H)cg[d];
+    clH[d] = (H)cl[d];
+  }
+  // deviations from the references the step kernel adds (in its arithmetic type)
+  const double rg = sizeof(S) == 8 ? a.r_ag : (double)a.pf.r_ag, rl = sizeof(S) == 8 ? a.r_al : (double)a.pf.r_al;
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const double w = L::w(q);
@@ -777,14 +926,23 @@ __global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *al
     double o[6];
     o[0] = w * (deg + 3.0 * vug + 4.5 * vug * vug - 1.5 * ug2);
     o[1] = w * ((q == 0 ? a.k0 * (0.0 - dPl) : dPl) + 3.0 * vul + 4.5 * vul * vul - 1.5 * ul2);
-    o[2] = feqS_dev<L, double>(q, ag, ug, ug2, a.r_ag);
-    o[3] = feqS_dev<L, double>(q, al, ul, ul2, a.r_al);
-    o[4] = feqS_dev<L, double>(q, 1.0, cg, cg2, 1.0);
-    o[5] = feqS_dev<L, double>(q, 1.0, cl, cl2, 1.0);
+    o[2] = feqS_dev<L, double>(q, ag, ug, ug2, rg);
+    o[3] = feqS_dev<L, double>(q, al, ul, ul2, rl);
+    o[4] = (double)beta_dev<L, H>(q, cgH);
+    o[5] = (double)beta_dev<L, H>(q, clH);
 #pragma unroll
-    for (int s = 0; s < 6; s++) Store<S>::template st<double>(base + (long long)(s * Q + q) * a.plane + i, o[s]);
+    for (int s = 0; s < (BS ? 4 : 6); s++)
+      Store<S>::template st<double>(base + (long long)(s * Q + q) * a.plane + i, o[s]);
   }
-  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  if (BS) {
+    // beta-stencil form: c of the initial state in the buffer the first step
+    // reads (1), evaluated at every q from the node's own c (beta_own)
+    H *cw = (H *)a.cfield + 2 * D * a.plane;
+    for (int d = 0; d < D; d++) {
+      cw[d * a.plane + i] = cgH[d];
+      cw[(D + d) * a.plane + i] = clH[d];
+    }
+  }
   H *held = (H *)a.held;
   held[i] = (H)0;
   held[a.plane + i] = (H)0;

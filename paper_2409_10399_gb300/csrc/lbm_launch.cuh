@@ -12,10 +12,17 @@ struct Launch {
   using L = Lattice<LAT>;
   // prec: 1 = FP32, 2 = FP16 store, 3 = FP64 deviations (0, the FP64
   // reference path, has its own launchers in lbm_ref_*.cu)
+  // bs: the beta-stencil form (StepArgs::cfield); every kernel below comes
+  // in both forms
+  template <bool BS>
+  static void step_form(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    if (prec == 3) k_step<L, double, double, BS><<<grid, block, smem, st>>>(a);
+    else if (prec == 1) k_step<L, float, float, BS><<<grid, block, smem, st>>>(a);
+    else k_step<L, __half, float, BS><<<grid, block, smem, st>>>(a);
+  }
   static cudaError_t step(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    if (prec == 3) k_step<L, double, double><<<grid, block, smem, st>>>(a);
-    else if (prec == 1) k_step<L, float, float><<<grid, block, smem, st>>>(a);
-    else k_step<L, __half, float><<<grid, block, smem, st>>>(a);
+    if (a.cfield) step_form<true>(prec, a, grid, block, smem, st);
+    else step_form<false>(prec, a, grid, block, smem, st);
     return cudaGetLastError();
   }
   static cudaError_t batch_step(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork, dim3 block,
@@ -25,23 +32,37 @@ struct Launch {
     else k_batch_step<L, __half, float><<<nwork, block, 0, st>>>(args, work, parity, latch);
     return cudaGetLastError();
   }
+  template <bool BS> static void moments_form(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
+    if (prec == 3) k_moments<L, double, double, BS><<<nblk, 256, 0, st>>>(ma, mode);
+    else if (prec == 1) k_moments<L, float, float, BS><<<nblk, 256, 0, st>>>(ma, mode);
+    else k_moments<L, __half, float, BS><<<nblk, 256, 0, st>>>(ma, mode);
+  }
   static cudaError_t moments(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
-    if (prec == 3) k_moments<L, double, double><<<nblk, 256, 0, st>>>(ma, mode);
-    else if (prec == 1) k_moments<L, float, float><<<nblk, 256, 0, st>>>(ma, mode);
-    else k_moments<L, __half, float><<<nblk, 256, 0, st>>>(ma, mode);
+    if (ma.s.cfield) moments_form<true>(prec, ma, mode, nblk, st);
+    else moments_form<false>(prec, ma, mode, nblk, st);
     return cudaGetLastError();
   }
+  template <bool BS> static void pops_form(int prec, const MomArgs &ma, int s, unsigned nblk, cudaStream_t st) {
+    if (prec == 0 || prec == 3) k_pops<L, double, double, BS><<<nblk, 256, 0, st>>>(ma, s);
+    else if (prec == 1) k_pops<L, float, float, BS><<<nblk, 256, 0, st>>>(ma, s);
+    else k_pops<L, __half, float, BS><<<nblk, 256, 0, st>>>(ma, s);
+  }
   static cudaError_t pops(int prec, const MomArgs &ma, int s, unsigned nblk, cudaStream_t st) {
-    if (prec == 0 || prec == 3) k_pops<L, double, double><<<nblk, 256, 0, st>>>(ma, s);
-    else if (prec == 1) k_pops<L, float, float><<<nblk, 256, 0, st>>>(ma, s);
-    else k_pops<L, __half, float><<<nblk, 256, 0, st>>>(ma, s);
+    if (ma.s.cfield) pops_form<true>(prec, ma, s, nblk, st);
+    else pops_form<false>(prec, ma, s, nblk, st);
     return cudaGetLastError();
+  }
+  template <bool BS>
+  static void init_form(int prec, const MomArgs &ma, const double *a, const double *ug, const double *ul,
+                        const double *pk, unsigned nblk, cudaStream_t st) {
+    if (prec == 3) k_init<L, double, BS><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    else if (prec == 1) k_init<L, float, BS><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    else k_init<L, __half, BS><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
   }
   static cudaError_t init(int prec, const MomArgs &ma, const double *a, const double *ug, const double *ul,
                           const double *pk, unsigned nblk, cudaStream_t st) {
-    if (prec == 3) k_init<L, double><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
-    else if (prec == 1) k_init<L, float><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
-    else k_init<L, __half><<<nblk, 256, 0, st>>>(ma, a, ug, ul, pk);
+    if (ma.s.cfield) init_form<true>(prec, ma, a, ug, ul, pk, nblk, st);
+    else init_form<false>(prec, ma, a, ug, ul, pk, nblk, st);
     return cudaGetLastError();
   }
 };
