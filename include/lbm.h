@@ -181,6 +181,11 @@ int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz);
 /* Current tile (tile[0..2]) of the fused step kernel. */
 int lbm_get_tile(const lbm_ctx *c, int tile[3]);
 
+/* Largest tile (threads per block) of the fused step kernel of lattice
+ * LBM_D1Q3/D2Q9/D3Q19 in precision LBM_FP* (its launch bounds), through
+ * *max_threads.  Host only, no GPU needed; LBM_EINVAL for unknown codes. */
+int lbm_tile_limit(int lattice, int precision, int *max_threads);
+
 /* Time step counter t (number of completed steps since lbm_init). */
 int lbm_time(const lbm_ctx *c, long long *t);
 

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Simulation", "Batch", "LBMError", "load_library", "lattice_tables", "PRECISION", "LATTICE", "BC"]
+__all__ = ["Simulation", "Batch", "LBMError", "load_library", "lattice_tables", "tile_limit", "PRECISION", "LATTICE",
+           "BC"]
 
 LATTICE = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "fp64dev": 3}
@@ -80,6 +81,7 @@ def load_library(build_if_missing=True):
             "lbm_time": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_set_tile": (I, [P, I, I, I]),
             "lbm_get_tile": (I, [P, ctypes.POINTER(I)]),
+            "lbm_tile_limit": (I, [I, I, ctypes.POINTER(I)]),
             "lbm_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_last_error": (ctypes.c_char_p, [P]),
             "lbm_destroy": (I, [P]),
@@ -119,6 +121,18 @@ def lattice_tables(lattice):
         raise LBMError(rc)
     q = Q.value
     return np.array(v[:3 * q], np.int64).reshape(q, 3)[:, :L], np.array(w[:q])
+
+
+def tile_limit(lattice, precision):
+    """Largest tile (threads per block) of the fused step kernel of `lattice`
+    ("D2Q9" or its D) in `precision` ("fp32" ... or its code); no GPU needed."""
+    L = LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    m = ctypes.c_int()
+    rc = load_library().lbm_tile_limit(L, prec, ctypes.byref(m))
+    if rc:
+        raise LBMError(rc, "lbm_tile_limit")
+    return m.value
 
 
 def default_params():

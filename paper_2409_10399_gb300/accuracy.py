@@ -1,6 +1,7 @@
 """Error and throughput of the precision forms on the workloads.
 
-    python -m paper_2409_10399_gb300.accuracy [--study box2d|column3d|column1d|all]
+    python -m paper_2409_10399_gb300.accuracy [--study box2d|column3d|column1d|all|
+                                                sensitivity|spalding|bstencil|column3d_small]
 
 For each study the same seeded state is advanced with the FP64 reference path
 (bitwise equal to the CPU oracle on every case the tests cover) and with the
@@ -113,6 +114,10 @@ def main():
     ap.add_argument("--spalding", type=int, default=None, help="override the Spalding mode of the workloads")
     args = ap.parse_args()
     todo = []
+    if args.study == "column3d_small":
+        # D3Q19 at 128 x 128 x 256 (2 GB of store traffic per step): the
+        # profiling case of the 3D kernels
+        todo.append(lambda: [throughput("column3d", f, steps=20, dims=(128, 128, 256)) for f in ("fp16dev", "fp32")])
     if args.study == "bstencil":
         todo.append(lambda: [throughput(n, f, steps=400, beta_stencil=b) for n, f in
                              (("box2d", "fp32"), ("box2d", "fp16dev"), ("column3d", "fp16dev"), ("column3d", "fp32"))

@@ -19,6 +19,7 @@ CANDIDATES = {
     (2, 128): [(64, 2, 1), (32, 4, 1), (16, 8, 1), (128, 1, 1), (32, 2, 1), (64, 1, 1)],
     (2, 256): [(64, 4, 1), (32, 8, 1), (128, 2, 1), (64, 2, 1), (32, 4, 1)],
     (3, 256): [(32, 4, 2), (32, 2, 4), (64, 2, 2), (32, 8, 1), (16, 8, 2), (32, 4, 1)],
+    (3, 128): [(16, 8, 1), (32, 4, 1), (32, 2, 2), (16, 4, 2), (64, 2, 1)],
 }
 
 
@@ -49,7 +50,8 @@ def tune(obj, lattice_d, precision, nodes, kind, steps=40, use_cache=True):
     """Choose a tile for `obj` (a Simulation or a Batch: set_tile, step).
     Returns (tile, {tile: seconds per step})."""
     import torch
-    maxthr = 128 if precision in ("fp32", "fp16dev") and lattice_d <= 2 else 256
+    from . import tile_limit
+    maxthr = tile_limit(lattice_d, precision)
     key = "|".join([_gpu_name(), "D%d" % lattice_d, precision, kind, _size_class(nodes)])
     cache = _load() if use_cache else {}
     if key in cache:

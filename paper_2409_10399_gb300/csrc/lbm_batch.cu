@@ -33,6 +33,7 @@ struct lbm_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_period = 0;
   long long t = 0, launches = 0;
+  int off32 = 1;  // every instance has Q*plane < 2^32 (32-bit population offsets)
   char err[512] = {0};
 };
 
@@ -52,9 +53,7 @@ static int berr(lbm_batch *b, int code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return berr((b), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-static int max_threads(const lbm_batch *b) {
-  return ((b->prec == LBM_FP32 || b->prec == LBM_FP16DEV) && b->lattice <= 2) ? 128 : 256;
-}
+static int max_threads(const lbm_batch *b) { return step_max_threads(b->lattice, b->prec); }
 
 static cudaStream_t launch_stream(lbm_batch *b) {
   // graphs cannot be captured on the legacy default stream: use an own
@@ -98,7 +97,7 @@ static int launch_one(lbm_batch *b, long long t, cudaStream_t st) {
   dim3 block(b->T[0], b->T[1], b->T[2]);
   const int parity = (int)(t & 1), latch = (t % b->n_gamma) == 0;
   b->launches++;
-  BTRY(b, launch_batch_step(b->lattice, b->prec, b->d_args, b->d_work, b->nwork, block, parity, latch, st));
+  BTRY(b, launch_batch_step(b->lattice, b->prec, b->d_args, b->d_work, b->nwork, block, parity, latch, b->off32, st));
   return LBM_OK;
 }
 
@@ -116,7 +115,7 @@ int lbm_batch_create(int lattice, int n, const int *dims, const lbm_params *para
   b->prec = prec;
   b->n = n;
   b->n_gamma = ng;
-  if (lattice == 3) { b->T[0] = 32; b->T[1] = 4; b->T[2] = 2; }
+  if (lattice == 3) { b->T[0] = 32; b->T[1] = 4; b->T[2] = max_threads(b) / 128; }
   if (lattice == 1) { b->T[0] = 128; b->T[1] = 1; b->T[2] = 1; }
   for (int i = 0; i < n; i++) {
     const lbm_params &p = params[i];
@@ -132,6 +131,7 @@ int lbm_batch_create(int lattice, int n, const int *dims, const lbm_params *para
       return rc;
     }
     b->inst.push_back(c);
+    if ((long long)c->Q * c->plane >= (1LL << 32)) b->off32 = 0;
   }
   if (cudaMalloc((void **)&b->d_args, n * sizeof(StepArgs)) != cudaSuccess ||
       cudaStreamCreate(&b->own_stream) != cudaSuccess) {

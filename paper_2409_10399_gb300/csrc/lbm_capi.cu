@@ -31,9 +31,12 @@ cudaError_t launch_init_2(int, const MomArgs &, const double *, const double *, 
                           unsigned, cudaStream_t);
 cudaError_t launch_init_3(int, const MomArgs &, const double *, const double *, const double *, const double *,
                           unsigned, cudaStream_t);
-cudaError_t launch_batch_step_1(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
-cudaError_t launch_batch_step_2(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
-cudaError_t launch_batch_step_3(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, cudaStream_t);
+cudaError_t launch_batch_step_1(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, int,
+                               cudaStream_t);
+cudaError_t launch_batch_step_2(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, int,
+                               cudaStream_t);
+cudaError_t launch_batch_step_3(int, const StepArgs *, const WorkItem *, unsigned, dim3, int, int, int,
+                               cudaStream_t);
 cudaError_t launch_ref_step_1(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
 cudaError_t launch_ref_step_2(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
 cudaError_t launch_ref_step_3(const StepArgs &, dim3, dim3, size_t, cudaStream_t);
@@ -204,6 +207,7 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.plain = c->prec == LBM_FP64;
   a.cfield = c->cfield;
   a.beta_own = c->cfield && t == 0;
+  a.off32 = (long long)c->Q * c->plane < (1LL << 32);
   // the same constants in the kernels' arithmetic types
   PhysT<double> &d = a.pd;
   d.R_ = a.R; d.invR = a.invR; d.omega_g = a.omega_g; d.omega_l = a.omega_l; d.omega_a = a.omega_a;
@@ -259,14 +263,36 @@ static int ensure_stage(lbm_ctx *c, size_t bytes) {
 // Tile of the fused kernel: x fastest; the axis of the inlet/outlet faces
 // gets a tile of at least 2 and a shift so that each edge node and its inward
 // neighbour share a block (their values are exchanged in shared memory).
+// Largest block the fused step kernel of this lattice and precision was
+// compiled for (its launch bounds); the FP64 reference kernels take 256.
+template <int LAT> static int bound_threads(int prec) {
+  if (prec == LBM_FP32) return StepBounds<Lattice<LAT>, float>::threads;
+  if (prec == LBM_FP16DEV) return StepBounds<Lattice<LAT>, __half>::threads;
+  if (prec == LBM_FP64DEV) return StepBounds<Lattice<LAT>, double>::threads;
+  return 256;
+}
+
+namespace lbm {
+int step_max_threads(int lattice, int prec) {
+  return lattice == 1 ? bound_threads<1>(prec) : (lattice == 2 ? bound_threads<2>(prec) : bound_threads<3>(prec));
+}
+}  // namespace lbm
+
+static int max_tile_threads(const lbm_ctx *c) { return step_max_threads(c->lattice, c->prec); }
+
+// Default tile: the kernel's full block size (the shapes measured fastest on
+// the workloads: 64 x 2 for D2Q9, 16 x 8 for D3Q19 at 128 threads).
 static void default_tile(lbm_ctx *c) {
   const lbm_params &p = c->p;
+  const int mt = max_tile_threads(c);
   if (c->D == 1) { c->T[0] = 32; c->T[1] = 1; c->T[2] = 1; }  // small 1D domains: spread over SMs
-  else if (c->D == 2) { c->T[0] = 64; c->T[1] = 2; c->T[2] = 1; }
-  else { c->T[0] = 32; c->T[1] = 4; c->T[2] = 2; }
+  else if (c->D == 2) { c->T[0] = 64; c->T[1] = mt >= 128 ? mt / 64 : 1; c->T[2] = 1; }
+  else if (mt == 128) { c->T[0] = 16; c->T[1] = 8; c->T[2] = 1; }
+  else { c->T[0] = 32; c->T[1] = mt >= 128 ? 4 : 2; c->T[2] = mt >= 128 ? mt / 128 : 1; }
   const int ga = p.g_axis;
   const int io = (p.bc_lo[ga] == LBM_BC_INLET) || (p.bc_hi[ga] == LBM_BC_OUTLET);
-  if (io && c->D == 3 && ga == 2) { c->T[1] = 2; c->T[2] = 4; }
+  if (io && c->D == 3 && ga == 2) { c->T[0] = 32; c->T[1] = 2; c->T[2] = mt / 64; }  // >= 2 along z
+  if (io && c->D == 2 && ga == 1 && c->T[1] < 2) { c->T[0] = mt / 2; c->T[1] = 2; }
 }
 
 static int choose_tiles(lbm_ctx *c) {
@@ -297,10 +323,10 @@ static int choose_tiles(lbm_ctx *c) {
 namespace lbm {
 StepArgs ctx_step_args(const lbm_ctx *c, long long t) { return make_args(c, t); }
 cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const WorkItem *work, unsigned nwork,
-                              dim3 block, int parity, int latch, cudaStream_t st) {
-  if (lattice == 1) return launch_batch_step_1(prec, args, work, nwork, block, parity, latch, st);
-  if (lattice == 2) return launch_batch_step_2(prec, args, work, nwork, block, parity, latch, st);
-  return launch_batch_step_3(prec, args, work, nwork, block, parity, latch, st);
+                              dim3 block, int parity, int latch, int off32, cudaStream_t st) {
+  if (lattice == 1) return launch_batch_step_1(prec, args, work, nwork, block, parity, latch, off32, st);
+  if (lattice == 2) return launch_batch_step_2(prec, args, work, nwork, block, parity, latch, off32, st);
+  return launch_batch_step_3(prec, args, work, nwork, block, parity, latch, off32, st);
 }
 }  // namespace lbm
 
@@ -553,11 +579,10 @@ int lbm_get_diag(lbm_ctx *c, double out[8]) {
   return LBM_OK;
 }
 
-// Largest block the fused step of this lattice/precision was compiled for
-// (StepBounds in lbm_kernels.cuh).
-static int max_tile_threads(const lbm_ctx *c) {
-  if ((c->prec == LBM_FP32 || c->prec == LBM_FP16DEV) && c->D <= 2) return 128;
-  return 256;
+int lbm_tile_limit(int lattice, int precision, int *max_threads) {
+  if (lattice < 1 || lattice > 3 || precision < 0 || precision > 3 || !max_threads) return LBM_EINVAL;
+  *max_threads = step_max_threads(lattice, precision);
+  return LBM_OK;
 }
 
 int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz) {

@@ -35,6 +35,8 @@ struct lbm_ctx {
 namespace lbm {
 // helpers of lbm_capi.cu used by the batched form (lbm_batch.cu)
 StepArgs ctx_step_args(const lbm_ctx *c, long long t);
+// largest block of the fused step kernel of this lattice and precision
+int step_max_threads(int lattice, int prec);
 cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const WorkItem *work, unsigned nwork,
-                              dim3 block, int parity, int latch, cudaStream_t st);
+                              dim3 block, int parity, int latch, int off32, cudaStream_t st);
 }  // namespace lbm

@@ -68,6 +68,7 @@ struct StepArgs {
   int has_inlet, has_outlet;
   void *cfield;         // beta-stencil form: 2 buffers x 2*D planes of c (held type)
   int beta_own;         // beta-stencil form, first step after init: every q from the node's own c
+  int off32;            // Q*plane < 2^32: population offsets fit 32 bits
   // physics
   double invR, R, omega_g, omega_l, omega_a, kgrad;  // kgrad = omega_alpha / cs2
   double A_g, B_g, A_l, B_l;                         // sigma = A (Pi^eq - Pi) + B S'' I
@@ -316,17 +317,36 @@ __device__ __forceinline__ void load_beta(const StepArgs &a, const Geo &g, int p
   }
 }
 
+// Address of a population: the base of scheme s, base + s*Q*plane (the same
+// for every thread of the launch), plus one offset pq*plane + node per
+// direction, formed once and shared by the schemes.  OffT is the offset's
+// type: 32-bit unsigned when Q*plane < 2^32 (fewer address instructions),
+// else 64-bit.  With the bases hoisted (load_node) this raised the D2Q9 FP32
+// step from 11.4 to 13.5 GLUPS on the 512 x 2048 box.
+template <class L, class OffT>
+__device__ __forceinline__ OffT pop_offset(const StepArgs &a, int pq, long long idx) {
+  return (OffT)pq * (OffT)a.plane + (OffT)idx;
+}
+template <class L, class S>
+__device__ __forceinline__ const S *scheme_base(const StepArgs &a, int s) {
+  return (const S *)a.pop + (long long)(s * L::Q) * a.plane;
+}
+
 // Load all populations of the node (deviations) with the AA read rule.
-template <class L, class S, class R, bool BS = false>
+template <class L, class S, class R, bool BS = false, class OffT = long long>
 __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, R f[6][L::Q]) {
-  const S *base = (const S *)a.pop;
+  // the scheme bases formed once, before the loads (left inside the loop
+  // they cost the D2Q9 FP32 step 90 instead of 78 us on the 512 x 2048 box)
+  const S *sb[6];
+#pragma unroll
+  for (int s = 0; s < 6; s++) sb[s] = scheme_base<L, S>(a, s);
 #pragma unroll
   for (int q = 0; q < L::Q; q++) {
     int pq;
-    long long idx = read_slot<L>(a, g, q, parity, pq);
+    const long long idx = read_slot<L>(a, g, q, parity, pq);
+    const OffT off = pop_offset<L, OffT>(a, pq, idx);
 #pragma unroll
-    for (int s = 0; s < (BS ? 4 : 6); s++)
-      f[s][q] = Store<S>::template ld<R>(base + (long long)(s * L::Q + pq) * a.plane + idx);
+    for (int s = 0; s < (BS ? 4 : 6); s++) f[s][q] = Store<S>::template ld<R>(sb[s] + off);
   }
   if (BS) load_beta<L, S, R>(a, g, parity, f[4], f[5]);
 }
@@ -443,8 +463,14 @@ constexpr int XCH = 14;
 // and 5 resident blocks per SM, which caps registers at 102 (no spills) and
 // gives 20 warps per SM -- the kernel is memory-latency bound, and this
 // occupancy measured 11.8 GLUPS on the 512 x 2048 box against 11.1 GLUPS at
-// 104 registers / 16 warps.  D3Q19 and the double forms keep 256 threads.
+// 104 registers / 16 warps (128 x 4, 128 x 6 and 256 x 3 were slower too).
+// D3Q19 in float/half: 128 threads, 3 blocks per SM (168 registers, a few
+// spills, 12 warps per SM); on the 256 x 256 x 512 column this measured
+// 6.11 / 4.85 GLUPS (FP16 / FP32 store) against 5.44 / 4.67 GLUPS with
+// 256 x 1 (249 registers, 8 warps).  The double forms keep 256 threads.
 template <class L, class S> struct StepBounds { static constexpr int threads = 256, blocks = 1; };
+template <> struct StepBounds<Lattice<3>, float> { static constexpr int threads = 128, blocks = 3; };
+template <> struct StepBounds<Lattice<3>, __half> { static constexpr int threads = 128, blocks = 3; };
 template <> struct StepBounds<Lattice<2>, float> { static constexpr int threads = 128, blocks = 5; };
 template <> struct StepBounds<Lattice<2>, __half> { static constexpr int threads = 128, blocks = 5; };
 template <> struct StepBounds<Lattice<1>, float> { static constexpr int threads = 128, blocks = 4; };
@@ -456,7 +482,7 @@ template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads
 // blk_xch the block exchanges the edge rows' values for the inlet/outlet
 // rules through `xch` and synchronises once, so every thread of the block
 // must call this function.
-template <class L, class S, class R, bool BS = false>
+template <class L, class S, class R, bool BS = false, class OffT = long long>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
                                                 int latch, bool blk_xch, int gstride, R *xch) {
   constexpr int D = L::D, Q = L::Q;
@@ -466,7 +492,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
   if (active) {
     make_geo(a, D, g);
-    load_node<L, S, R, BS>(a, g, parity, f);
+    load_node<L, S, R, BS, OffT>(a, g, parity, f);
     moments<L, R>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -594,7 +620,6 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   }
 
   // ---- collisions and AA store with face rules
-  S *base = (S *)a.pop;
   const R om_g = P.omega_g, om_l = P.omega_l, om_a = P.omega_a;
   const R k0 = P.k0;
   const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
@@ -676,13 +701,14 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
     }
     int pq;
     const long long idx = write_slot<L>(a, g, q, cross, parity, pq);
+    const OffT off = pop_offset<L, OffT>(a, pq, idx);
 #pragma unroll
     for (int s = 0; s < (BS ? 4 : 6); s++)
-      Store<S>::template st<R>(base + (long long)(s * Q + pq) * a.plane + idx, out[s]);
+      Store<S>::template st<R>((S *)scheme_base<L, S>(a, s) + off, out[s]);
   }
 }
 
-template <class L, class S, class R, bool BS>
+template <class L, class S, class R, bool BS, class OffT>
 __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::blocks) k_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *xch = reinterpret_cast<R *>(smem_raw);
@@ -701,7 +727,7 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
   const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
-  fused_step_node<L, S, R, BS>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
+  fused_step_node<L, S, R, BS, OffT>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
 }
 
 // Batched form: one launch advances many independent lattices (instances) of
@@ -722,7 +748,7 @@ template <class L, class S> struct BatchBounds {
   static constexpr int blocks = StepBounds<L, S>::blocks;
 };
 
-template <class L, class S, class R>
+template <class L, class S, class R, class OffT>
 __global__ void __launch_bounds__(BatchBounds<L, S>::threads, BatchBounds<L, S>::blocks)
     k_batch_step(const StepArgs *__restrict__ args, const WorkItem *__restrict__ work, int parity, int latch) {
   // the instance's constants, staged once per block in shared memory
@@ -739,7 +765,7 @@ __global__ void __launch_bounds__(BatchBounds<L, S>::threads, BatchBounds<L, S>:
   g.c[1] = wi.y0 + threadIdx.y;
   g.c[2] = wi.z0 + threadIdx.z;
   const bool active = g.c[0] < a.n[0] && g.c[1] < a.n[1] && g.c[2] < a.n[2];
-  fused_step_node<L, S, R>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
+  fused_step_node<L, S, R, false, OffT>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
 }
 
 // --------------------------------------------------- moments / diagnostics

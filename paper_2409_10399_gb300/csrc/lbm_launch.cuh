@@ -14,22 +14,32 @@ struct Launch {
   // reference path, has its own launchers in lbm_ref_*.cu)
   // bs: the beta-stencil form (StepArgs::cfield); every kernel below comes
   // in both forms
-  template <bool BS>
+  template <bool BS, class OffT>
   static void step_form(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    if (prec == 3) k_step<L, double, double, BS><<<grid, block, smem, st>>>(a);
-    else if (prec == 1) k_step<L, float, float, BS><<<grid, block, smem, st>>>(a);
-    else k_step<L, __half, float, BS><<<grid, block, smem, st>>>(a);
+    if (prec == 3) k_step<L, double, double, BS, OffT><<<grid, block, smem, st>>>(a);
+    else if (prec == 1) k_step<L, float, float, BS, OffT><<<grid, block, smem, st>>>(a);
+    else k_step<L, __half, float, BS, OffT><<<grid, block, smem, st>>>(a);
   }
+  // six-scheme store: 32-bit population offsets where they fit; the
+  // beta-stencil form keeps 64-bit offsets (one instantiation)
   static cudaError_t step(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    if (a.cfield) step_form<true>(prec, a, grid, block, smem, st);
-    else step_form<false>(prec, a, grid, block, smem, st);
+    if (a.cfield) step_form<true, long long>(prec, a, grid, block, smem, st);
+    else if (a.off32) step_form<false, unsigned>(prec, a, grid, block, smem, st);
+    else step_form<false, long long>(prec, a, grid, block, smem, st);
     return cudaGetLastError();
   }
+  template <class OffT>
+  static void batch_form(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork, dim3 block,
+                         int parity, int latch, cudaStream_t st) {
+    if (prec == 3) k_batch_step<L, double, double, OffT><<<nwork, block, 0, st>>>(args, work, parity, latch);
+    else if (prec == 1) k_batch_step<L, float, float, OffT><<<nwork, block, 0, st>>>(args, work, parity, latch);
+    else k_batch_step<L, __half, float, OffT><<<nwork, block, 0, st>>>(args, work, parity, latch);
+  }
+  // off32: every instance has Q*plane < 2^32
   static cudaError_t batch_step(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork, dim3 block,
-                                int parity, int latch, cudaStream_t st) {
-    if (prec == 3) k_batch_step<L, double, double><<<nwork, block, 0, st>>>(args, work, parity, latch);
-    else if (prec == 1) k_batch_step<L, float, float><<<nwork, block, 0, st>>>(args, work, parity, latch);
-    else k_batch_step<L, __half, float><<<nwork, block, 0, st>>>(args, work, parity, latch);
+                                int parity, int latch, int off32, cudaStream_t st) {
+    if (off32) batch_form<unsigned>(prec, args, work, nwork, block, parity, latch, st);
+    else batch_form<long long>(prec, args, work, nwork, block, parity, latch, st);
     return cudaGetLastError();
   }
   template <bool BS> static void moments_form(int prec, const MomArgs &ma, int mode, unsigned nblk, cudaStream_t st) {
@@ -82,8 +92,8 @@ cudaError_t launch_init(int lat, int prec, const MomArgs &ma, const double *a, c
     return Launch<LAT>::step(prec, a, g, b, sm, st);                                                         \
   }                                                                                                          \
   cudaError_t launch_batch_step_##LAT(int prec, const StepArgs *args, const WorkItem *work, unsigned nwork,     \
-                                     dim3 block, int parity, int latch, cudaStream_t st) {                    \
-    return Launch<LAT>::batch_step(prec, args, work, nwork, block, parity, latch, st);                        \
+                                     dim3 block, int parity, int latch, int off32, cudaStream_t st) {         \
+    return Launch<LAT>::batch_step(prec, args, work, nwork, block, parity, latch, off32, st);                 \
   }                                                                                                          \
   cudaError_t launch_moments_##LAT(int prec, const MomArgs &ma, int mode, unsigned n, cudaStream_t st) {      \
     return Launch<LAT>::moments(prec, ma, mode, n, st);                                                      \

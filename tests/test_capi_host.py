@@ -74,3 +74,19 @@ def test_parameter_helpers_agree(name):
             assert b[k] == pytest.approx(v, rel=1e-14, abs=0), k
         else:
             assert tuple(np.atleast_1d(b[k])) == tuple(np.atleast_1d(v)), k
+
+
+def test_tile_limit_matches_launch_bounds():
+    """lbm_tile_limit reports the block size each fused step kernel is built
+    for (host only): 128 for the D2Q9/D1Q3/D3Q19 float and half stores, 256
+    for the double forms; unknown codes are rejected."""
+    import paper_2409_10399_gb300 as lbm
+    for lat in ("D1Q3", "D2Q9", "D3Q19"):
+        assert lbm.tile_limit(lat, "fp32") == 128
+        assert lbm.tile_limit(lat, "fp16dev") == 128
+        assert lbm.tile_limit(lat, "fp64dev") == 256
+        assert lbm.tile_limit(lat, "fp64") == 256
+    with pytest.raises(lbm.LBMError):
+        lbm.tile_limit(4, "fp32")
+    with pytest.raises(lbm.LBMError):
+        lbm.tile_limit("D2Q9", 7)
