@@ -63,3 +63,17 @@ def lattice_params(physics):
     out["kappa_I"] = kh
     out["kappa_W"] = kh if ph.get("wall_friction") else 0.0
     return out
+
+
+def diffusive_scaling(base, eps):
+    """Lattice parameters at mesh spacing eps = lambda/L under the diffusive
+    scaling of Sec. 2.1.2 (time step tau/T = eps^2): the relaxation rates stay
+    (lattice viscosities and the alpha diffusivity are the continuum ones),
+    g_hat = eps^3 g and K_hat_I = eps K_I (so kappa_hat_I, kappa_hat_W scale
+    with eps).  `base` holds the continuum values under the same keys
+    (g_hat = g, kappa_I = K_I, kappa_W = K_W)."""
+    p = dict(base)
+    p["g_hat"] = base.get("g_hat", 0.0) * eps ** 3
+    p["kappa_I"] = base.get("kappa_I", 0.0) * eps
+    p["kappa_W"] = base.get("kappa_W", 0.0) * eps
+    return p

@@ -34,3 +34,13 @@ def lattice_params(physics, precision=None, diag_every=0, drift_limit=0.0):
     out["diag_every"] = diag_every
     out["drift_limit"] = drift_limit
     return out
+
+
+def diffusive_scaling(base, eps):
+    """Parameters at mesh spacing eps under the diffusive scaling of Sec.
+    2.1.2 (tau/T = eps^2): relaxation rates unchanged, buoyancy eps^3, drag
+    coefficients eps (the continuum values are given under the lattice keys)."""
+    out = dict(base)
+    for key, power in (("g_hat", 3), ("kappa_I", 1), ("kappa_W", 1)):
+        out[key] = base.get(key, 0.0) * eps ** power
+    return out
