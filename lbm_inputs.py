@@ -101,6 +101,20 @@ def fields_smooth1d(n, eps, U=0.64):
     return dict(alpha_g=a, u_g=ug[None, :], u_l=ul[None, :], p_k=np.full(n, CS2_PK))
 
 
+def fields_smooth2d(n, eps, U=0.64):
+    """Smooth doubly periodic 2D state on the unit square (cell-centred n x n
+    nodes): alpha_g = 0.3 + 0.05 sin(2 pi x) sin(2 pi y), both phases in the
+    divergence-free Taylor-Green field eps U (sin 2 pi x cos 2 pi y,
+    -cos 2 pi x sin 2 pi y) (so the mixture flux is divergence-free), p_k
+    uniform.  Vector fields (2, n*n), x fastest."""
+    c = (np.arange(n) + 0.5) / n
+    y, x = np.meshgrid(c, c, indexing="ij")
+    a = (0.3 + 0.05 * np.sin(2.0 * np.pi * x) * np.sin(2.0 * np.pi * y)).reshape(-1)
+    u = eps * U * np.stack([np.sin(2.0 * np.pi * x) * np.cos(2.0 * np.pi * y),
+                            -np.cos(2.0 * np.pi * x) * np.sin(2.0 * np.pi * y)]).reshape(2, -1)
+    return dict(alpha_g=a, u_g=u.copy(), u_l=u.copy(), p_k=np.full(n * n, CS2_PK))
+
+
 def rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 

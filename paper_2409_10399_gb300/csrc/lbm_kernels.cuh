@@ -262,13 +262,24 @@ template <> struct Rn<double> {
 // side and the beta-stencil form on the read side, and both must give the
 // same bits.
 template <class L, class R>
-__device__ __forceinline__ R beta_dev(int q, const R c[3]) {
+__device__ __forceinline__ R beta_c2(const R c[3]) {
   R c2 = R(0);
 #pragma unroll
   for (int d = 0; d < L::D; d++) c2 = Rn<R>::fma(c[d], c[d], c2);
-  const R vc = vdot<L, R>(q, c);
-  const R t = Rn<R>::fma(Rn<R>::mul(R(4.5), vc), vc, Rn<R>::fma(R(3), vc, Rn<R>::mul(R(-1.5), c2)));
-  return Rn<R>::mul((R)L::w(q), t);
+  return c2;
+}
+// even part w_q (9/2 (v.c)^2 - 3/2 c^2), the same for q and opp(q); vc = v_q . c
+template <class L, class R>
+__device__ __forceinline__ R beta_even(int q, const R c[3], R c2, R &vc) {
+  vc = vdot<L, R>(q, c);
+  const R t = Rn<R>::fma(Rn<R>::mul(R(4.5), vc), vc, Rn<R>::mul(R(-1.5), c2));
+  return Rn<R>::mul(wq<L, R>(q), t);
+}
+template <class L, class R>
+__device__ __forceinline__ R beta_dev(int q, const R c[3]) {
+  R vc;
+  const R x = beta_even<L, R>(q, c, beta_c2<L, R>(c), vc);
+  return Rn<R>::fma(aq<L, R>(q), vc, x);
 }
 
 template <class L, class R>
@@ -440,13 +451,14 @@ __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], M
 
 
 // f^eq(alpha, u)_q - w_q*r with the quadratic term of Eq. (equilibrium),
-// grouped as w [(alpha - r) + alpha (3 v.u + 9/2 (v.u)^2 - 3/2 u^2)] so that
+// grouped as w [(alpha - r) + alpha (9/2 (v.u)^2 - 3/2 u^2)] + alpha a_q v.u
+// (a_q = w_q / cs2, see lbm_lattice.cuh) so that
 // alpha = r (the beta schemes, r = 1) loses nothing to cancellation.
 template <class L, class R>
 __device__ __forceinline__ R feqS_dv(int q, R alpha, R alpha_dev, const R u[3], R uu) {
-  const R w = (R)L::w(q);
+  const R w = wq<L, R>(q);
   const R vu = vdot<L, R>(q, u);
-  return w * (alpha_dev + alpha * (R(3) * vu + R(4.5) * vu * vu - R(1.5) * uu));
+  return w * (alpha_dev + alpha * (R(4.5) * vu * vu - R(1.5) * uu)) + alpha * (aq<L, R>(q) * vu);
 }
 // the same with alpha - r formed here
 template <class L, class R>
@@ -621,30 +633,22 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
 
   // ---- collisions and AA store with face rules
   const R om_g = P.omega_g, om_l = P.omega_l, om_a = P.omega_a;
-  const R k0 = P.k0;
   const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
   const R deq_g = a.spalding == 2 ? m.dalg : m.dag, deq_l = a.spalding == 2 ? m.dall : m.dal;
   const R rag = P.r_ag, ral = P.r_al;
-  // equilibrium offsets of f_I^eq - w: rest and moving directions, Eq. (eta)
-  const R eI_g0 = m.deg, eI_gq = m.deg;                 // phi_g = 1
-  const R eI_l0 = m.del + k0 * (m.del - dPl), eI_lq = dPl;
-  const R eL_g0 = Spp_g * P.eta0_g, eL_gq = Spp_g * P.psi_g;
-  const R eL_l0 = Spp_l * P.eta0_l, eL_lq = Spp_l * P.psi_l;
+  // Eq. (eta) for the moving directions: eta_q(phi) = phi, so the offsets of
+  // f_I^eq - w are eps_g - 1 (phi_g = 1) and phi eps_l - 1 = dPl, and f_L's
+  // is S psi.  The rest direction takes what makes the zeroth moments exact
+  // with the weights in use (sum w_q = 1): w_0 eta_0 = 1 - (1 - w_0) phi, i.e.
+  // w_0 f_I^eq(0) - w_0 = (eps_l - 1) - (1 - w_0) dPl for the liquid, and
+  // w_0 f_L(0) = S - (1 - w_0) psi S; (1 - w_0) x is formed as x - w_0 x so
+  // that no rounded 1 - w_0 biases them.
+  const R eL_gq = Spp_g * P.psi_g, eL_lq = Spp_l * P.psi_l;
+  const R c2g = BS ? R(0) : beta_c2<L, R>(cg), c2l = BS ? R(0) : beta_c2<L, R>(cl);
 
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const R w = (R)L::w(q);
-    const R vug = vdot<L, R>(q, m.ug), vul = vdot<L, R>(q, m.ul);
-    const R vGg = vdot<L, R>(q, Gg), vGl = vdot<L, R>(q, Gl);
-    R out[6];
-    out[0] = f[0][q] + om_g * (w * ((q == 0 ? eI_g0 : eI_gq) + R(3) * vug + R(4.5) * vug * vug - R(1.5) * ug2) - f[0][q]) +
-             w * ((q == 0 ? eL_g0 : eL_gq) + R(3) * vGg);
-    out[1] = f[1][q] + om_l * (w * ((q == 0 ? eI_l0 : eI_lq) + R(3) * vul + R(4.5) * vul * vul - R(1.5) * ul2) - f[1][q]) +
-             w * ((q == 0 ? eL_l0 : eL_lq) + R(3) * vGl);
-    out[2] = f[2][q] + om_a * (feqS_dv<L, R>(q, aeq_g, deq_g, m.ug, ug2) - f[2][q]);
-    out[3] = f[3][q] + om_a * (feqS_dv<L, R>(q, aeq_l, deq_l, m.ul, ul2) - f[3][q]);
-    if (!BS) beta_pair<L, R>(q, cg, cl, out[4], out[5]);
-
+  // face rules of direction q (walls, Tables 1-2) and its AA store
+  auto finish = [&](const int q, R out[6]) {
+    const R w = wq<L, R>(q);
     const bool cross = crosses<L>(g, q, +1);
     if (cross) {
       const int rule = face_rule<L>(a, g, q);
@@ -653,8 +657,8 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         // Table 1: f_g, f_l BB(I) (Eq. (BB): -2 w v.u^B/cs2), f_alpha EQ(S)
         // Dirichlet, f_beta EQ(S) with beta and c extrapolated full-way.
         const R vq = (R)(gax == 0 ? L::v(q, 0) : (gax == 1 ? L::v(q, 1) : L::v(q, 2)));
-        out[0] -= R(6) * w * vq * P.ugIN;
-        out[1] -= R(6) * w * vq * P.ulIN;
+        out[0] -= R(2) * aq<L, R>(q) * vq * P.ugIN;
+        out[1] -= R(2) * aq<L, R>(q) * vq * P.ulIN;
         R uin[3], lin[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
@@ -705,6 +709,57 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
 #pragma unroll
     for (int s = 0; s < (BS ? 4 : 6); s++)
       Store<S>::template st<R>((S *)scheme_base<L, S>(a, s) + off, out[s]);
+  };
+
+  // Collisions, direction by direction: the rest direction alone, the moving
+  // ones in pairs (q, opp q), whose equilibria share their even part
+  // w_q (...) and differ in the sign of their odd part a_q v_q . u.
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const int qo = L::opp(q);
+    if (q == 0) {
+      const R w = wq<L, R>(0);
+      R out[6];
+      const R rest_Il = m.del - (dPl - w * dPl);
+      const R rest_Lg = Spp_g - P.psi_g * (Spp_g - w * Spp_g), rest_Ll = Spp_l - P.psi_l * (Spp_l - w * Spp_l);
+      out[0] = f[0][0] + om_g * (w * (m.deg - R(1.5) * ug2) - f[0][0]) + rest_Lg;
+      out[1] = f[1][0] + om_l * ((rest_Il - w * (R(1.5) * ul2)) - f[1][0]) + rest_Ll;
+      out[2] = f[2][0] + om_a * (feqS_dv<L, R>(0, aeq_g, deq_g, m.ug, ug2) - f[2][0]);
+      out[3] = f[3][0] + om_a * (feqS_dv<L, R>(0, aeq_l, deq_l, m.ul, ul2) - f[3][0]);
+      if (!BS) beta_pair<L, R>(0, cg, cl, out[4], out[5]);
+      finish(0, out);
+    } else if (q < qo) {
+      const R w = wq<L, R>(q), aw = aq<L, R>(q);
+      const R vug = vdot<L, R>(q, m.ug), vul = vdot<L, R>(q, m.ul);
+      const R vGg = vdot<L, R>(q, Gg), vGl = vdot<L, R>(q, Gl);
+      const R qug = R(4.5) * vug * vug - R(1.5) * ug2, qul = R(4.5) * vul * vul - R(1.5) * ul2;
+      // f_g, f_l: even / odd parts of f_I^eq - w and of f_L
+      const R Xg = w * (m.deg + qug), Yg = aw * vug, Xl = w * (dPl + qul), Yl = aw * vul;
+      const R Fg = w * eL_gq, Hg = aw * vGg, Fl = w * eL_lq, Hl = aw * vGl;
+      // f_alpha (the split of feqS_dv)
+      const R Xag = w * (deq_g + aeq_g * qug), Yag = aeq_g * (aw * vug);
+      const R Xal = w * (deq_l + aeq_l * qul), Yal = aeq_l * (aw * vul);
+      R oa[6], ob[6];
+      oa[0] = f[0][q] + om_g * ((Xg + Yg) - f[0][q]) + (Fg + Hg);
+      ob[0] = f[0][qo] + om_g * ((Xg - Yg) - f[0][qo]) + (Fg - Hg);
+      oa[1] = f[1][q] + om_l * ((Xl + Yl) - f[1][q]) + (Fl + Hl);
+      ob[1] = f[1][qo] + om_l * ((Xl - Yl) - f[1][qo]) + (Fl - Hl);
+      oa[2] = f[2][q] + om_a * ((Xag + Yag) - f[2][q]);
+      ob[2] = f[2][qo] + om_a * ((Xag - Yag) - f[2][qo]);
+      oa[3] = f[3][q] + om_a * ((Xal + Yal) - f[3][q]);
+      ob[3] = f[3][qo] + om_a * ((Xal - Yal) - f[3][qo]);
+      if (!BS) {
+        // beta_dev of q and opp(q) from one even part (v_opp . c = -v_q . c exactly)
+        R vcg, vcl;
+        const R xg = beta_even<L, R>(q, cg, c2g, vcg), xl = beta_even<L, R>(q, cl, c2l, vcl);
+        oa[4] = Rn<R>::fma(aw, vcg, xg);
+        ob[4] = Rn<R>::fma(aw, -vcg, xg);
+        oa[5] = Rn<R>::fma(aw, vcl, xl);
+        ob[5] = Rn<R>::fma(aw, -vcl, xl);
+      }
+      finish(q, oa);
+      finish(qo, ob);
+    }
   }
 }
 

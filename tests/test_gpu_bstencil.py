@@ -9,7 +9,7 @@ arithmetic, from c held in the kernel's own type (FP32, FP64 deviations): the
 initial state (where every q comes from the node's own c) is bitwise that of
 the six-scheme store.  The rest of the step is the same source compiled into
 another kernel, where the compiler may fuse multiply-adds differently, so
-later states agree to rounding: node by node within 1e-6 (FP32) or 1e-13
+later states agree to rounding: node by node within 2e-6 (FP32) or 1e-13
 (FP64 deviations) of each field's scale (S = 1 - beta with the parity tests'
 absolute floor), at every step count checked (t = 0,
 1, 2, odd and even end states, whose state sits in the other AA layout and c
@@ -29,7 +29,7 @@ from test_gpu_parity import CASES, S_ATOL, assert_parity, case_fields, run_pair
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l")
-ROUND = {"fp32": 1e-6, "fp64dev": 1e-13}
+ROUND = {"fp32": 2e-6, "fp64dev": 1e-13}
 
 
 def _close(x, y, tol, what, atol=0.0):
