@@ -271,6 +271,68 @@ int lbm_batch_destroy(lbm_batch *b);
 int lbm_diag_populations_noalloc(int lattice, int spalding_mode, const double *pops, long long n_nodes,
                                  double *out, int out_on_device, void *stream);
 
+/* ---- Learned surrogate (not in the paper) ---------------------------------
+ * A factorised Fourier neural operator that maps a 2D state to its change
+ * over a fixed number of LBM steps (64 in the surrogate workload), trained on
+ * trajectories the library's own LBM produces; the plain LBM step is its
+ * reference and its fallback.  Model (channels C, K modes per axis, L layers;
+ * state channels padded to 16):
+ *   h_0 = W_in x + b_in;  h_l = GELU(W_l h + b_l + S^x_l h + S^y_l h);
+ *   y = W_out h_L + b_out;  next = now + s_out * y.
+ * S^x projects every row onto the truncated real Fourier basis of the x axis
+ * (cos k x, sin k x, k < K), mixes the channels of each mode with complex
+ * weights A_k + i B_k, and projects back; S^y likewise along y.  Every
+ * contraction is a BF16 matrix product with FP32 accumulation; parameters,
+ * gradients and Adam moments are FP32.  2,115,920 parameters at C = 64,
+ * K = 32, L = 4.
+ *
+ * The state is six FP64 device planes of nx*ny values, [alpha_g][u_g,x]
+ * [u_g,y][u_l,x][u_l,y][p_k], node x + nx*y (the layout of lbm_get_moments
+ * for D2Q9).  Inputs are normalised with (mean, std_in) per channel and the
+ * model's output is scaled by std_out (lbm_fno_set_norm).  All work runs on
+ * the model's stream; the calls that return a number synchronise it. */
+typedef struct lbm_fno lbm_fno;
+/* nx, ny: multiples of 16; channels: a multiple of 16; modes: a multiple of 8
+ * with 2*modes <= nx, ny; 1 <= layers <= 16.  Parameters start at zero
+ * (lbm_fno_set_params sets them).  LBM_EINVAL / LBM_ENOMEM. */
+int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno **out);
+int lbm_fno_num_params(const lbm_fno *f, long long *n);
+/* Host FP32 arrays of lbm_fno_num_params values, in this order: W_in (C x 16),
+ * b_in (C); per layer W (C x C), b (C), A_x, B_x, A_y, B_y (K x C x C each,
+ * [k][c_out][c_in]); W_out (16 x C), b_out (16). */
+int lbm_fno_set_params(lbm_fno *f, const float *host, long long n);
+int lbm_fno_get_params(const lbm_fno *f, float *host, long long n);
+int lbm_fno_get_grads(const lbm_fno *f, float *host, long long n);
+int lbm_fno_zero_grads(lbm_fno *f);
+int lbm_fno_set_norm(lbm_fno *f, const float mean[6], const float std_in[6], const float std_out[6]);
+int lbm_fno_set_stream(lbm_fno *f, void *cuda_stream);
+/* One training sample: forward from `now`, loss = mean over the six state
+ * channels and the nodes of (y - (next - now)/std_out)^2 (returned in *loss),
+ * and its gradient added to the accumulated gradients.  `now`, `next`: FP64
+ * device states. */
+int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double *loss);
+/* Adam step (Kingma & Ba, bias-corrected) with the accumulated gradients
+ * times grad_scale, then gradients zeroed and the BF16 weights refreshed. */
+int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, float grad_scale);
+/* Surrogate step: next = now + std_out * model(now) (device states, distinct
+ * buffers).  *drift = relative change of the per-phase volumes sum(alpha_g)
+ * and sum(1 - alpha_g) (the larger; infinite if non-finite); *ok = drift <=
+ * max_drift.  A caller that gets ok = 0 advances the state with the LBM
+ * instead (the surrogate's fallback). */
+int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok);
+int lbm_fno_launch_count(const lbm_fno *f, long long *n);
+const char *lbm_fno_last_error(const lbm_fno *f);
+int lbm_fno_destroy(lbm_fno *f);
+/* The surrogate's matrix product alone (for tests and measurement):
+ * C[b] = alpha op(A[b]) op(B[b]) + beta C[b], b < batch, BF16 A and B (device,
+ * row-major; op(A) = A^T when ta, stored K x M), FP32 (out_f32) or BF16 C.
+ * M, N, K multiples of 16, leading dimensions multiples of 8, pointers 32-byte
+ * aligned.  ksplit > 1 splits K over blocks with FP32 atomics (needs out_f32
+ * and beta = 1).  Enqueued on `stream`; LBM_EINVAL for bad shapes. */
+int lbm_fno_gemm(int ta, int tb, int M, int N, int K, float alpha, const void *A, int lda, long long sA,
+                 const void *B, int ldb, long long sB, float beta, void *C, int ldc, long long sC, int batch,
+                 int out_f32, int ksplit, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

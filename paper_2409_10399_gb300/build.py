@@ -13,7 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["lbm_capi.cu", "lbm_d1q3.cu", "lbm_d2q9.cu", "lbm_d3q19.cu",
-           "lbm_ref_d1q3.cu", "lbm_ref_d2q9.cu", "lbm_ref_d3q19.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
+           "lbm_ref_d1q3.cu", "lbm_ref_d2q9.cu", "lbm_ref_d3q19.cu", "lbm_noalloc.cu", "lbm_batch.cu",
+           "lbm_fno.cu"]
 # the FP64 reference path is compiled without floating-point contraction;
 # the fast paths use approximate single-precision division and square root
 FAST = ["-prec-div=false", "-prec-sqrt=false"]

@@ -1,0 +1,251 @@
+// Kernels of the learned surrogate (a factorised Fourier neural operator that
+// advances the 2D state by 64 LBM steps): one batched, strided BF16 matrix
+// product with FP32 accumulation (tensor-core fragments), and the FP32
+// elementwise operations around it.  Not part of the paper's method: the
+// surrogate is judged against, and falls back to, the lattice Boltzmann step.
+#pragma once
+#include <cuda_bf16.h>
+#include <mma.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace fno {
+
+typedef __nv_bfloat16 bf16;
+
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b], b < batch.  op(A) is M x K,
+// op(B) is K x N.  Row-major storage: A is M x K (lda >= K), or K x M
+// (lda >= M) when ta; B is K x N (ldb >= N), or N x K (ldb >= K) when tb;
+// C is M x N (ldc >= N), float or bf16.  M, N, K multiples of 16, leading
+// dimensions multiples of 8, bases 32-byte aligned (checked by the host).
+// ksplit > 1 splits K into chunks of kchunk (a multiple of 32) over blocks,
+// each adding alpha times its partial product into a float C with atomics
+// (C += alpha op(A) op(B); beta is not applied).
+struct GemmArgs {
+  const bf16 *A, *B;
+  void *C;
+  int M, N, K, lda, ldb, ldc;
+  long long sA, sB, sC;  // batch strides (elements)
+  float alpha, beta;
+  int ksplit, kchunk;
+};
+
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+template <bool TA, bool TB, class OutT>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+  using namespace nvcuda;
+  // A tile: [GBM][GBK] (TA: [GBK][GBM]); B tile: [GBK][GBN] (TB: [GBN][GBK])
+  constexpr int A_ROWS = TA ? GBK : GBM, A_COLS = TA ? GBM : GBK;
+  constexpr int B_ROWS = TB ? GBN : GBK, B_COLS = TB ? GBK : GBN;
+  __shared__ __align__(32) bf16 sA[A_ROWS][A_COLS + GPAD];
+  __shared__ __align__(32) bf16 sB[B_ROWS][B_COLS + GPAD];
+  __shared__ __align__(32) float sC[GBM][GBN + 4];
+
+  const int b = blockIdx.z / g.ksplit, split = blockIdx.z % g.ksplit;
+  const int kbeg = split * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const bf16 *A = g.A + (long long)b * g.sA;
+  const bf16 *B = g.B + (long long)b * g.sB;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // 2 x 2 warps of 32 x 32
+
+  typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16,
+                         typename std::conditional<TA, wmma::col_major, wmma::row_major>::type> FragA;
+  typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16,
+                         typename std::conditional<TB, wmma::col_major, wmma::row_major>::type> FragB;
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 2; j++) wmma::fill_fragment(acc[i][j], 0.0f);
+
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+    // global -> shared in 16-byte vectors (8 bf16), zero outside the matrix
+#pragma unroll
+    for (int v = tid; v < A_ROWS * A_COLS / 8; v += 128) {
+      const int r = v / (A_COLS / 8), c = (v % (A_COLS / 8)) * 8;
+      const int gr = (TA ? k0 : m0) + r, gc = (TA ? m0 : k0) + c;
+      const int mi = TA ? gc : gr, ki = TA ? gr : gc;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (mi < g.M && ki < kend) val = *reinterpret_cast<const uint4 *>(A + (long long)gr * g.lda + gc);
+      *reinterpret_cast<uint4 *>(&sA[r][c]) = val;
+    }
+#pragma unroll
+    for (int v = tid; v < B_ROWS * B_COLS / 8; v += 128) {
+      const int r = v / (B_COLS / 8), c = (v % (B_COLS / 8)) * 8;
+      const int gr = (TB ? n0 : k0) + r, gc = (TB ? k0 : n0) + c;
+      const int ni = TB ? gr : gc, ki = TB ? gc : gr;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (ni < g.N && ki < kend) val = *reinterpret_cast<const uint4 *>(B + (long long)gr * g.ldb + gc);
+      *reinterpret_cast<uint4 *>(&sB[r][c]) = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      FragA fa[2];
+      FragB fb[2];
+#pragma unroll
+      for (int i = 0; i < 2; i++) {
+        const bf16 *pa = TA ? &sA[kk][wm + 16 * i] : &sA[wm + 16 * i][kk];
+        wmma::load_matrix_sync(fa[i], pa, A_COLS + GPAD);
+        const bf16 *pb = TB ? &sB[wn + 16 * i][kk] : &sB[kk][wn + 16 * i];
+        wmma::load_matrix_sync(fb[i], pb, B_COLS + GPAD);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+      wmma::store_matrix_sync(&sC[wm + 16 * i][wn + 16 * j], acc[i][j], GBN + 4, wmma::mem_row_major);
+  __syncthreads();
+  OutT *C = reinterpret_cast<OutT *>(g.C) + (long long)b * g.sC;
+  for (int v = tid; v < GBM * GBN; v += 128) {
+    const int r = v / GBN, c = v % GBN;
+    const int gr = m0 + r, gc = n0 + c;
+    if (gr < g.M && gc < g.N) {
+      OutT *p = C + (long long)gr * g.ldc + gc;
+      if constexpr (std::is_same<OutT, float>::value) {
+        if (g.ksplit > 1) {
+          atomicAdd(p, g.alpha * sC[r][c]);
+          continue;
+        }
+      }
+      float val = g.alpha * sC[r][c];
+      if (g.beta != 0.0f) val += g.beta * (float)(*p);
+      *p = (OutT)val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- elementwise
+
+__device__ __forceinline__ float gelu(float z) {
+  // tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+  const float k = 0.7978845608028654f;
+  return 0.5f * z * (1.0f + tanhf(k * (z + 0.044715f * z * z * z)));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float k = 0.7978845608028654f;
+  const float u = k * (z + 0.044715f * z * z * z);
+  const float t = tanhf(u);
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
+}
+
+// z[c][p] += bias[c]; h = act ? gelu(z) : z, as bf16 (z keeps the biased value)
+__global__ void k_bias_act(float *z, const float *bias, bf16 *h, int C, long long P, int act) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)C * P) return;
+  const int c = (int)(i / P);
+  const float v = z[i] + bias[c];
+  z[i] = v;
+  h[i] = __float2bfloat16(act ? gelu(v) : v);
+}
+
+// dz = act ? dh * gelu'(z) : dh  (float and bf16 copies)
+__global__ void k_act_back(const float *dh, const float *z, float *dz, bf16 *dz16, long long n, int act) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = act ? dh[i] * gelu_grad(z[i]) : dh[i];
+  dz[i] = v;
+  dz16[i] = __float2bfloat16(v);
+}
+
+// db[c] += sum_p dz[c][p]: one block per channel, fixed-order tree reduction
+__global__ void k_bias_grad(const float *dz, float *db, long long P) {
+  __shared__ float s[256];
+  const int c = blockIdx.x;
+  float acc = 0.0f;
+  for (long long p = threadIdx.x; p < P; p += blockDim.x) acc += dz[(long long)c * P + p];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] += s[0];
+}
+
+// squared error of the first `cv` of C channels: d = 2 (y - t) / (cv P)
+// (zero on padding channels), per-block partial sums of (y - t)^2 in part
+__global__ void k_mse(const float *y, const float *t, float *d, bf16 *d16, int cv, long long P, long long n,
+                      double *part) {
+  __shared__ double s[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e2 = 0.0;
+  if (i < n) {
+    const int c = (int)(i / P);
+    float g = 0.0f;
+    if (c < cv) {
+      const float e = y[i] - t[i];
+      e2 = (double)e * e;
+      g = 2.0f * e / (float)((double)cv * P);
+    }
+    d[i] = g;
+    d16[i] = __float2bfloat16(g);
+  }
+  s[threadIdx.x] = e2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// Adam (Kingma & Ba) on FP32 master parameters, bias-corrected step size lr_t
+// (gradient scaled by gscale, e.g. 1 / samples accumulated)
+__global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr_t, float b1, float b2,
+                       float eps, float gscale) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i] * gscale;
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr_t * mi / (sqrtf(vi) + eps);
+}
+
+__global__ void k_to_bf16(const float *x, bf16 *y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// Complex channel mixing of mode k as a real 2C x 2C matrix:
+// W[k] = [[A_k, -B_k], [B_k, A_k]] (rows: cosine block, then sine block)
+__global__ void k_assemble_complex(const float *A, const float *B, bf16 *W, int C, int K) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = 4LL * C * C;
+  if (i >= per * K) return;
+  const int k = (int)(i / per);
+  const int r = (int)((i % per) / (2 * C)), c = (int)(i % (2 * C));
+  const int ri = r % C, ci = c % C;
+  const float a = A[(long long)k * C * C + (long long)ri * C + ci], bb = B[(long long)k * C * C + (long long)ri * C + ci];
+  float val;
+  if (r < C) val = c < C ? a : -bb;
+  else val = c < C ? bb : a;
+  W[i] = __float2bfloat16(val);
+}
+
+// gradient of the real 2C x 2C matrices back onto A_k, B_k:
+// dA = dW11 + dW22, dB = dW21 - dW12
+__global__ void k_fold_complex(const float *dW, float *dA, float *dB, int C, int K) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)K * C * C) return;
+  const int k = (int)(i / ((long long)C * C));
+  const int r = (int)((i / C) % C), c = (int)(i % C);
+  const float *W = dW + (long long)k * 4 * C * C;
+  const int L = 2 * C;
+  dA[i] += W[r * L + c] + W[(r + C) * L + c + C];
+  dB[i] += W[(r + C) * L + c] - W[r * L + c + C];
+}
+
+}  // namespace fno

@@ -1,0 +1,685 @@
+// Learned surrogate of the 2D step: a factorised Fourier neural operator
+// (per-axis spectral convolutions with truncated real-DFT bases) that maps the
+// state (alpha_g, u_g, u_l, p_k) to its increment over 64 LBM steps.  Not in
+// the paper; the plain lattice Boltzmann step is its reference and fallback.
+//
+// Model, channels C, K modes per axis, L layers (state channels padded to 16):
+//   h_0 = W_in x + b_in
+//   h_l = GELU(W_l h_{l-1} + b_l + S^x_l(h_{l-1}) + S^y_l(h_{l-1})),  l = 1..L
+//   y   = W_out h_L + b_out,   x_next = x + s_out * y   (s_out per channel)
+// S^x: coefficients H = h B_x (B_x: n_x x 2K, columns cos k x, sin k x for
+// k < K, interleaved), per mode the complex channel mixing
+// [O_c; O_s] = [[A_k, -B_k], [B_k, A_k]] [H_c; H_s], back with the inverse
+// basis (B_x scaled by 1/n_x for k = 0, 2/n_x otherwise).  S^y likewise
+// along y.  Every contraction is a BF16 matrix product with FP32
+// accumulation (fno_kernels.cuh); activations of the backward pass are kept
+// per layer (z in FP32, h and the spectral coefficients in BF16).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "fno_kernels.cuh"
+
+using fno::bf16;
+
+namespace {
+
+struct Off {  // offsets of one model's parameters in the FP32 parameter buffer
+  long long W_in, b_in, W_out, b_out;
+  std::vector<long long> W, b, Ax, Bx, Ay, By;
+  long long total;
+};
+
+Off layout(int C, int K, int L, int cin, int cout) {
+  Off o;
+  long long at = 0;
+  o.W_in = at; at += (long long)C * cin;
+  o.b_in = at; at += C;
+  for (int l = 0; l < L; l++) {
+    o.W.push_back(at); at += (long long)C * C;
+    o.b.push_back(at); at += C;
+    o.Ax.push_back(at); at += (long long)K * C * C;
+    o.Bx.push_back(at); at += (long long)K * C * C;
+    o.Ay.push_back(at); at += (long long)K * C * C;
+    o.By.push_back(at); at += (long long)K * C * C;
+  }
+  o.W_out = at; at += (long long)cout * C;
+  o.b_out = at; at += cout;
+  o.total = at;
+  return o;
+}
+
+}  // namespace
+
+struct lbm_fno {
+  int nx, ny, C, K, L, cin = 16, cout = 16, cv = 6;
+  long long P;
+  Off off;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  long long adam_t = 0;
+  bf16 *W_in16 = nullptr, *W_out16 = nullptr, *W16 = nullptr, *Wfx16 = nullptr, *Wfy16 = nullptr;
+  bf16 *Bx = nullptr, *Bxi = nullptr, *By = nullptr, *Byi = nullptr;
+  bf16 *x16 = nullptr, *h16 = nullptr, *Hx16 = nullptr, *Hy16 = nullptr, *O16 = nullptr, *y16 = nullptr;
+  float *z = nullptr, *zin = nullptr, *y = nullptr, *tgt = nullptr;
+  float *dy = nullptr, *dh = nullptr, *dz = nullptr, *dWf = nullptr;
+  bf16 *dy16 = nullptr, *dz16 = nullptr, *dO16 = nullptr, *dH16 = nullptr;
+  double *part = nullptr, *h_part = nullptr, *red = nullptr, *h_red = nullptr;
+  float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
+  cudaStream_t stream = 0;
+  long long launches = 0;
+  char err[512] = {0};
+};
+
+static int ferr(lbm_fno *f, int code, const char *fmt, ...) {
+  if (f) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(f->err, sizeof f->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define FTRY(f, call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return ferr((f), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ GEMM
+
+struct G {
+  const bf16 *A, *B;
+  void *C;
+  int M, N, K, lda, ldb, ldc;
+  long long sA = 0, sB = 0, sC = 0;
+  int batch = 1;
+  float alpha = 1.0f, beta = 0.0f;
+  bool ta = false, tb = false, out_f32 = true;
+  int ksplit = 1;  // > 1: K split over blocks, FP32 atomic accumulation (beta must be 1)
+};
+
+template <bool TA, bool TB, class OutT>
+static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
+  fno::k_gemm<TA, TB, OutT><<<grid, 128, 0, st>>>(a);
+}
+
+static cudaError_t gemm(const G &g, cudaStream_t st) {
+  if (g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1) return cudaErrorInvalidValue;
+  if (((uintptr_t)g.A | (uintptr_t)g.B | (uintptr_t)g.C) & 31) return cudaErrorMisalignedAddress;
+  if (g.ksplit > 1 && !g.out_f32) return cudaErrorInvalidValue;
+  int ks = g.ksplit < 1 ? 1 : g.ksplit;
+  int kchunk = ((g.K + ks - 1) / ks + fno::GBK - 1) / fno::GBK * fno::GBK;
+  ks = (g.K + kchunk - 1) / kchunk;
+  if ((long long)g.batch * ks > 65535) return cudaErrorInvalidValue;
+  fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk};
+  dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
+  if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
+  else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
+  else if (g.tb) g.out_f32 ? launch_gemm_t<false, true, float>(a, grid, st) : launch_gemm_t<false, true, bf16>(a, grid, st);
+  else g.out_f32 ? launch_gemm_t<false, false, float>(a, grid, st) : launch_gemm_t<false, false, bf16>(a, grid, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ kernels of the state interface
+
+// per-channel scales of the state interface
+struct Norm {
+  float mean[6], std_in[6], std_out[6];
+};
+
+// x16[c][p] = (state[c][p] - mean[c]) / std_in[c] for c < 6, zero for padding
+__global__ void k_pack_state(const double *state, bf16 *x16, int cin, long long P, Norm nm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)cin * P) return;
+  const int c = (int)(i / P);
+  float v = 0.0f;
+  if (c < 6) v = (float)((state[i] - (double)nm.mean[c]) / (double)nm.std_in[c]);
+  x16[i] = __float2bfloat16(v);
+}
+
+// target increment in the model's units: t[c][p] = (next - now) / std_out[c]
+__global__ void k_pack_target(const double *now, const double *next, float *t, int cout, long long P, Norm nm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)cout * P) return;
+  const int c = (int)(i / P);
+  t[i] = c < 6 ? (float)((next[i] - now[i]) / (double)nm.std_out[c]) : 0.0f;
+}
+
+// next = now + std_out * y (FP64 state, FP32 increment)
+__global__ void k_unpack(const double *now, const float *y, double *next, long long P, Norm nm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * P) return;
+  const int c = (int)(i / P);
+  next[i] = now[i] + (double)nm.std_out[c] * (double)y[i];
+}
+
+// FP64 sums of alpha_g over the field (block partials), for the mass check
+__global__ void k_sum(const double *a, long long n, double *part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += a[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// ------------------------------------------------------------------ model pieces
+
+static int refresh_weights(lbm_fno *f) {
+  const int C = f->C, K = f->K, L = f->L;
+  cudaStream_t st = f->stream;
+  fno::k_to_bf16<<<nblk((long long)C * f->cin), 256, 0, st>>>(f->p + f->off.W_in, f->W_in16, (long long)C * f->cin);
+  fno::k_to_bf16<<<nblk((long long)f->cout * C), 256, 0, st>>>(f->p + f->off.W_out, f->W_out16, (long long)f->cout * C);
+  f->launches += 2;
+  for (int l = 0; l < L; l++) {
+    fno::k_to_bf16<<<nblk((long long)C * C), 256, 0, st>>>(f->p + f->off.W[l], f->W16 + (long long)l * C * C,
+                                                          (long long)C * C);
+    const long long wf = (long long)K * 4 * C * C;
+    fno::k_assemble_complex<<<nblk(wf), 256, 0, st>>>(f->p + f->off.Ax[l], f->p + f->off.Bx[l], f->Wfx16 + l * wf, C, K);
+    fno::k_assemble_complex<<<nblk(wf), 256, 0, st>>>(f->p + f->off.Ay[l], f->p + f->off.By[l], f->Wfy16 + l * wf, C, K);
+    f->launches += 3;
+  }
+  FTRY(f, cudaGetLastError());
+  return LBM_OK;
+}
+
+#define GTRY(f, gg)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = gemm((gg), (f)->stream);                                            \
+    (f)->launches++;                                                                     \
+    if (e_ != cudaSuccess) return ferr((f), LBM_ECUDA, "gemm %s (line %d): %s", #gg, __LINE__, cudaGetErrorString(e_)); \
+  } while (0)
+
+// z += S^x(h): h is C x (ny x nx) bf16, z is C x (ny x nx) float
+static int spec_x(lbm_fno *f, const bf16 *h, bf16 *Hx, const bf16 *Wf, float *z) {
+  const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  G a;  // Hx (2K x C ny) = B_x^T h^T
+  a.A = f->Bx; a.ta = true; a.lda = K2;
+  a.B = h; a.tb = true; a.ldb = nx;
+  a.C = Hx; a.out_f32 = false; a.ldc = C * ny;
+  a.M = K2; a.N = C * ny; a.K = nx;
+  GTRY(f, a);
+  G b;  // per mode: O_k (2C x ny) = Wf_k (2C x 2C) H_k
+  b.A = Wf; b.lda = 2 * C; b.sA = 4LL * C * C;
+  b.B = Hx; b.ldb = ny; b.sB = 2LL * C * ny;
+  b.C = f->O16; b.out_f32 = false; b.ldc = ny; b.sC = 2LL * C * ny;
+  b.M = 2 * C; b.N = ny; b.K = 2 * C; b.batch = f->K;
+  GTRY(f, b);
+  G c;  // z (C ny x nx) += O^T Bxi^T
+  c.A = f->O16; c.ta = true; c.lda = C * ny;
+  c.B = f->Bxi; c.tb = true; c.ldb = K2;
+  c.C = z; c.ldc = nx; c.beta = 1.0f;
+  c.M = C * ny; c.N = nx; c.K = K2;
+  GTRY(f, c);
+  return LBM_OK;
+}
+
+// z += S^y(h); Hy is [2K][C][nx]
+static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z) {
+  const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  const long long P = f->P;
+  G a;  // per channel c: Hy[:, c, :] (2K x nx) = B_y^T h[c]
+  a.A = f->By; a.ta = true; a.lda = K2;
+  a.B = h; a.ldb = nx; a.sB = P;
+  a.C = Hy; a.out_f32 = false; a.ldc = C * nx; a.sC = nx;
+  a.M = K2; a.N = nx; a.K = ny; a.batch = C;
+  GTRY(f, a);
+  G b;  // per mode: O_k (2C x nx) = Wf_k H_k, rows (j C + c)
+  b.A = Wf; b.lda = 2 * C; b.sA = 4LL * C * C;
+  b.B = Hy; b.ldb = nx; b.sB = 2LL * C * nx;
+  b.C = f->O16; b.out_f32 = false; b.ldc = nx; b.sC = 2LL * C * nx;
+  b.M = 2 * C; b.N = nx; b.K = 2 * C; b.batch = f->K;
+  GTRY(f, b);
+  G c;  // per channel: z[c] (ny x nx) += Byi O[:, c, :]
+  c.A = f->Byi; c.lda = K2;
+  c.B = f->O16; c.ldb = C * nx; c.sB = nx;
+  c.C = z; c.ldc = nx; c.sC = P; c.beta = 1.0f;
+  c.M = ny; c.N = nx; c.K = K2; c.batch = C;
+  GTRY(f, c);
+  return LBM_OK;
+}
+
+// forward from f->x16 to f->y (cout x P float); keeps h_l, z_l, Hx_l, Hy_l
+static int forward(lbm_fno *f) {
+  const int C = f->C, L = f->L;
+  const long long P = f->P, CP = (long long)C * P;
+  const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
+  G a;  // lifting: zin = W_in x
+  a.A = f->W_in16; a.lda = f->cin; a.B = f->x16; a.ldb = (int)P; a.C = f->zin; a.ldc = (int)P;
+  a.M = C; a.N = (int)P; a.K = f->cin;
+  GTRY(f, a);
+  fno::k_bias_act<<<nblk(CP), 256, 0, f->stream>>>(f->zin, f->p + f->off.b_in, f->h16, C, P, 0);
+  f->launches++;
+  for (int l = 0; l < L; l++) {
+    const bf16 *h = f->h16 + l * CP;
+    float *z = f->z + l * CP;
+    G w;  // z = W_l h
+    w.A = f->W16 + (long long)l * C * C; w.lda = C; w.B = h; w.ldb = (int)P; w.C = z; w.ldc = (int)P;
+    w.M = C; w.N = (int)P; w.K = C;
+    GTRY(f, w);
+    int rc = spec_x(f, h, f->Hx16 + l * hx, f->Wfx16 + l * wf, z);
+    if (rc) return rc;
+    rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z);
+    if (rc) return rc;
+    fno::k_bias_act<<<nblk(CP), 256, 0, f->stream>>>(z, f->p + f->off.b[l], f->h16 + (l + 1) * CP, C, P, 1);
+    f->launches++;
+  }
+  G o;  // y = W_out h_L (+ b_out)
+  o.A = f->W_out16; o.lda = C; o.B = f->h16 + L * CP; o.ldb = (int)P; o.C = f->y; o.ldc = (int)P;
+  o.M = f->cout; o.N = (int)P; o.K = C;
+  GTRY(f, o);
+  fno::k_bias_act<<<nblk((long long)f->cout * P), 256, 0, f->stream>>>(f->y, f->p + f->off.b_out, f->y16, f->cout, P, 0);
+  f->launches++;
+  FTRY(f, cudaGetLastError());
+  return LBM_OK;
+}
+
+// dh_prev += (S^x)^T dz; gradients of A_x, B_x into the parameter gradient
+static int spec_x_back(lbm_fno *f, const bf16 *dz16, const bf16 *Hx, const bf16 *Wf, float *dh, float *gA,
+                       float *gB) {
+  const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  G a;  // dO (2K x C ny) = Bxi^T dz^T
+  a.A = f->Bxi; a.ta = true; a.lda = K2;
+  a.B = dz16; a.tb = true; a.ldb = nx;
+  a.C = f->dO16; a.out_f32 = false; a.ldc = C * ny;
+  a.M = K2; a.N = C * ny; a.K = nx;
+  GTRY(f, a);
+  G w;  // dWf_k (2C x 2C) = dO_k H_k^T
+  w.A = f->dO16; w.lda = ny; w.sA = 2LL * C * ny;
+  w.B = Hx; w.tb = true; w.ldb = ny; w.sB = 2LL * C * ny;
+  w.C = f->dWf; w.ldc = 2 * C; w.sC = 4LL * C * C;
+  w.M = 2 * C; w.N = 2 * C; w.K = ny; w.batch = f->K;
+  GTRY(f, w);
+  fno::k_fold_complex<<<nblk((long long)f->K * C * C), 256, 0, f->stream>>>(f->dWf, gA, gB, C, f->K);
+  f->launches++;
+  G b;  // dH_k = Wf_k^T dO_k
+  b.A = Wf; b.ta = true; b.lda = 2 * C; b.sA = 4LL * C * C;
+  b.B = f->dO16; b.ldb = ny; b.sB = 2LL * C * ny;
+  b.C = f->dH16; b.out_f32 = false; b.ldc = ny; b.sC = 2LL * C * ny;
+  b.M = 2 * C; b.N = ny; b.K = 2 * C; b.batch = f->K;
+  GTRY(f, b);
+  G c;  // dh (C ny x nx) += dH^T B_x^T
+  c.A = f->dH16; c.ta = true; c.lda = C * ny;
+  c.B = f->Bx; c.tb = true; c.ldb = K2;
+  c.C = dh; c.ldc = nx; c.beta = 1.0f;
+  c.M = C * ny; c.N = nx; c.K = K2;
+  GTRY(f, c);
+  return LBM_OK;
+}
+
+static int spec_y_back(lbm_fno *f, const bf16 *dz16, const bf16 *Hy, const bf16 *Wf, float *dh, float *gA,
+                       float *gB) {
+  const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  const long long P = f->P;
+  G a;  // per channel: dO[:, c, :] = Byi^T dz[c]
+  a.A = f->Byi; a.ta = true; a.lda = K2;
+  a.B = dz16; a.ldb = nx; a.sB = P;
+  a.C = f->dO16; a.out_f32 = false; a.ldc = C * nx; a.sC = nx;
+  a.M = K2; a.N = nx; a.K = ny; a.batch = C;
+  GTRY(f, a);
+  G w;  // dWf_k = dO_k H_k^T
+  w.A = f->dO16; w.lda = nx; w.sA = 2LL * C * nx;
+  w.B = Hy; w.tb = true; w.ldb = nx; w.sB = 2LL * C * nx;
+  w.C = f->dWf; w.ldc = 2 * C; w.sC = 4LL * C * C;
+  w.M = 2 * C; w.N = 2 * C; w.K = nx; w.batch = f->K;
+  GTRY(f, w);
+  fno::k_fold_complex<<<nblk((long long)f->K * C * C), 256, 0, f->stream>>>(f->dWf, gA, gB, C, f->K);
+  f->launches++;
+  G b;  // dH_k = Wf_k^T dO_k
+  b.A = Wf; b.ta = true; b.lda = 2 * C; b.sA = 4LL * C * C;
+  b.B = f->dO16; b.ldb = nx; b.sB = 2LL * C * nx;
+  b.C = f->dH16; b.out_f32 = false; b.ldc = nx; b.sC = 2LL * C * nx;
+  b.M = 2 * C; b.N = nx; b.K = 2 * C; b.batch = f->K;
+  GTRY(f, b);
+  G c;  // per channel: dh[c] += B_y dH[:, c, :]
+  c.A = f->By; c.lda = K2;
+  c.B = f->dH16; c.ldb = C * nx; c.sB = nx;
+  c.C = dh; c.ldc = nx; c.sC = P; c.beta = 1.0f;
+  c.M = ny; c.N = nx; c.K = K2; c.batch = C;
+  GTRY(f, c);
+  return LBM_OK;
+}
+
+// split of the long contractions over pixels (weight gradients)
+static int ksplit_for(long long K) {
+  const long long chunk = 4096;
+  long long s = (K + chunk - 1) / chunk;
+  return (int)(s < 1 ? 1 : (s > 512 ? 512 : s));
+}
+
+// loss of f->y against f->tgt; gradients accumulated into f->g
+static int backward(lbm_fno *f, double *loss) {
+  const int C = f->C, L = f->L;
+  const long long P = f->P, CP = (long long)C * P, nout = (long long)f->cout * P;
+  const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
+  const unsigned nb = nblk(nout);
+  fno::k_mse<<<nb, 256, 0, f->stream>>>(f->y, f->tgt, f->dy, f->dy16, f->cv, P, nout, f->part);
+  f->launches++;
+  FTRY(f, cudaMemcpyAsync(f->h_part, f->part, nb * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  G go;  // dW_out += dy h_L^T
+  go.A = f->dy16; go.lda = (int)P; go.B = f->h16 + L * CP; go.tb = true; go.ldb = (int)P;
+  go.C = f->g + f->off.W_out; go.ldc = C; go.beta = 1.0f; go.ksplit = ksplit_for(P);
+  go.M = f->cout; go.N = C; go.K = (int)P;
+  GTRY(f, go);
+  fno::k_bias_grad<<<f->cout, 256, 0, f->stream>>>(f->dy, f->g + f->off.b_out, P);
+  f->launches++;
+  G gh;  // dh = W_out^T dy
+  gh.A = f->W_out16; gh.ta = true; gh.lda = C; gh.B = f->dy16; gh.ldb = (int)P; gh.C = f->dh; gh.ldc = (int)P;
+  gh.M = C; gh.N = (int)P; gh.K = f->cout;
+  GTRY(f, gh);
+  for (int l = L - 1; l >= 0; l--) {
+    fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, f->z + l * CP, f->dz, f->dz16, CP, 1);
+    fno::k_bias_grad<<<C, 256, 0, f->stream>>>(f->dz, f->g + f->off.b[l], P);
+    f->launches += 2;
+    const bf16 *h = f->h16 + l * CP;
+    G gw;  // dW_l += dz h^T
+    gw.A = f->dz16; gw.lda = (int)P; gw.B = h; gw.tb = true; gw.ldb = (int)P;
+    gw.C = f->g + f->off.W[l]; gw.ldc = C; gw.beta = 1.0f; gw.ksplit = ksplit_for(P);
+    gw.M = C; gw.N = C; gw.K = (int)P;
+    GTRY(f, gw);
+    G gd;  // dh = W_l^T dz (the previous dh is consumed)
+    gd.A = f->W16 + (long long)l * C * C; gd.ta = true; gd.lda = C; gd.B = f->dz16; gd.ldb = (int)P;
+    gd.C = f->dh; gd.ldc = (int)P; gd.M = C; gd.N = (int)P; gd.K = C;
+    GTRY(f, gd);
+    int rc = spec_x_back(f, f->dz16, f->Hx16 + l * hx, f->Wfx16 + l * wf, f->dh, f->g + f->off.Ax[l],
+                         f->g + f->off.Bx[l]);
+    if (rc) return rc;
+    rc = spec_y_back(f, f->dz16, f->Hy16 + l * hy, f->Wfy16 + l * wf, f->dh, f->g + f->off.Ay[l],
+                     f->g + f->off.By[l]);
+    if (rc) return rc;
+  }
+  // lifting (no activation)
+  fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, f->zin, f->dz, f->dz16, CP, 0);
+  fno::k_bias_grad<<<C, 256, 0, f->stream>>>(f->dz, f->g + f->off.b_in, P);
+  f->launches += 2;
+  G gi;  // dW_in += dz x^T
+  gi.A = f->dz16; gi.lda = (int)P; gi.B = f->x16; gi.tb = true; gi.ldb = (int)P;
+  gi.C = f->g + f->off.W_in; gi.ldc = f->cin; gi.beta = 1.0f; gi.ksplit = ksplit_for(P);
+  gi.M = C; gi.N = f->cin; gi.K = (int)P;
+  GTRY(f, gi);
+  FTRY(f, cudaStreamSynchronize(f->stream));
+  double s = 0.0;
+  for (unsigned i = 0; i < nb; i++) s += f->h_part[i];
+  if (loss) *loss = s / ((double)f->cv * P);
+  FTRY(f, cudaGetLastError());
+  return LBM_OK;
+}
+
+// ------------------------------------------------------------------ set-up
+
+// Truncated real-DFT bases of an axis of n points and K modes, columns
+// (cos 0, sin 0, cos 1, sin 1, ...): forward b[x][2k+j], inverse scaled so
+// that a signal with modes < K is reproduced (1/n for k = 0, 2/n otherwise).
+static void basis(int n, int K, std::vector<float> &fw, std::vector<float> &inv) {
+  fw.assign((size_t)n * 2 * K, 0.0f);
+  inv.assign((size_t)n * 2 * K, 0.0f);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int x = 0; x < n; x++)
+    for (int k = 0; k < K; k++) {
+      const double ph = two_pi * (double)k * (double)x / (double)n;
+      const double c = cos(ph), s = sin(ph), sc = (k == 0 ? 1.0 : 2.0) / (double)n;
+      fw[(size_t)x * 2 * K + 2 * k] = (float)c;
+      fw[(size_t)x * 2 * K + 2 * k + 1] = (float)s;
+      inv[(size_t)x * 2 * K + 2 * k] = (float)(c * sc);
+      inv[(size_t)x * 2 * K + 2 * k + 1] = (float)(s * sc);
+    }
+}
+
+static int upload_bf16(lbm_fno *f, const std::vector<float> &h, bf16 *dst) {
+  float *tmp = nullptr;
+  FTRY(f, cudaMalloc((void **)&tmp, h.size() * sizeof(float)));
+  cudaError_t e = cudaMemcpy(tmp, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    fno::k_to_bf16<<<nblk((long long)h.size()), 256>>>(tmp, dst, (long long)h.size());
+    e = cudaDeviceSynchronize();
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) return ferr(f, LBM_ECUDA, "upload: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_fno_destroy(lbm_fno *f) {
+  if (!f) return LBM_OK;
+  cudaStreamSynchronize(f->stream);
+  void *bufs[] = {f->p, f->g, f->m, f->v, f->W_in16, f->W_out16, f->W16, f->Wfx16, f->Wfy16, f->Bx, f->Bxi, f->By,
+                  f->Byi, f->x16, f->h16, f->Hx16, f->Hy16, f->O16, f->y16, f->z, f->zin, f->y, f->tgt, f->dy, f->dh,
+                  f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (f->h_part) cudaFreeHost(f->h_part);
+  if (f->h_red) cudaFreeHost(f->h_red);
+  delete f;
+  return LBM_OK;
+}
+
+int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (nx < 16 || ny < 16 || nx % 16 || ny % 16 || channels < 16 || channels % 16 || modes < 8 || modes % 8 ||
+      2 * modes > nx || 2 * modes > ny || layers < 1 || layers > 16 || (long long)nx * ny >= (1LL << 31) / 64)
+    return LBM_EINVAL;
+  lbm_fno *f = new (std::nothrow) lbm_fno();
+  if (!f) return LBM_ENOMEM;
+  f->nx = nx; f->ny = ny; f->C = channels; f->K = modes; f->L = layers;
+  f->P = (long long)nx * ny;
+  f->off = layout(channels, modes, layers, f->cin, f->cout);
+  const long long P = f->P, C = channels, CP = C * P, K2 = 2LL * modes;
+  const long long hmax = K2 * C * (nx > ny ? nx : ny), wf = (long long)modes * 4 * C * C;
+  const long long np = f->off.total;
+  struct A { void **p; long long bytes; } al[] = {
+      {(void **)&f->p, np * 4}, {(void **)&f->g, np * 4}, {(void **)&f->m, np * 4}, {(void **)&f->v, np * 4},
+      {(void **)&f->W_in16, C * f->cin * 2}, {(void **)&f->W_out16, f->cout * C * 2},
+      {(void **)&f->W16, layers * C * C * 2}, {(void **)&f->Wfx16, layers * wf * 2},
+      {(void **)&f->Wfy16, layers * wf * 2}, {(void **)&f->Bx, nx * K2 * 2},
+      {(void **)&f->Bxi, nx * K2 * 2}, {(void **)&f->By, ny * K2 * 2},
+      {(void **)&f->Byi, ny * K2 * 2}, {(void **)&f->x16, f->cin * P * 2},
+      {(void **)&f->h16, (layers + 1) * CP * 2}, {(void **)&f->Hx16, layers * K2 * C * ny * 2},
+      {(void **)&f->Hy16, layers * K2 * C * nx * 2}, {(void **)&f->O16, hmax * 2},
+      {(void **)&f->y16, f->cout * P * 2}, {(void **)&f->z, layers * CP * 4},
+      {(void **)&f->zin, CP * 4}, {(void **)&f->y, f->cout * P * 4},
+      {(void **)&f->tgt, f->cout * P * 4}, {(void **)&f->dy, f->cout * P * 4},
+      {(void **)&f->dh, CP * 4}, {(void **)&f->dz, CP * 4}, {(void **)&f->dWf, wf * 4},
+      {(void **)&f->dy16, f->cout * P * 2}, {(void **)&f->dz16, CP * 2},
+      {(void **)&f->dO16, hmax * 2}, {(void **)&f->dH16, hmax * 2},
+      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 2048 * 8}};
+  for (auto &a : al) {
+    if (cudaMalloc(a.p, (size_t)a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      lbm_fno_destroy(f);
+      return LBM_ENOMEM;
+    }
+  }
+  if (cudaMallocHost((void **)&f->h_part, (size_t)nblk((long long)f->cout * P) * 8) != cudaSuccess ||
+      cudaMallocHost((void **)&f->h_red, 2048 * 8) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_fno_destroy(f);
+    return LBM_ENOMEM;
+  }
+  cudaMemset(f->p, 0, np * 4);
+  cudaMemset(f->g, 0, np * 4);
+  cudaMemset(f->m, 0, np * 4);
+  cudaMemset(f->v, 0, np * 4);
+  std::vector<float> fw, inv;
+  basis(nx, modes, fw, inv);
+  int rc = upload_bf16(f, fw, f->Bx);
+  if (!rc) rc = upload_bf16(f, inv, f->Bxi);
+  if (!rc) {
+    basis(ny, modes, fw, inv);
+    rc = upload_bf16(f, fw, f->By);
+  }
+  if (!rc) rc = upload_bf16(f, inv, f->Byi);
+  if (!rc) rc = refresh_weights(f);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = LBM_ECUDA;
+  if (rc) {
+    lbm_fno_destroy(f);
+    return rc;
+  }
+  *out = f;
+  return LBM_OK;
+}
+
+int lbm_fno_num_params(const lbm_fno *f, long long *n) {
+  if (!f || !n) return LBM_EINVAL;
+  *n = f->off.total;
+  return LBM_OK;
+}
+
+int lbm_fno_set_stream(lbm_fno *f, void *stream) {
+  if (!f) return LBM_EINVAL;
+  f->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_fno_set_params(lbm_fno *f, const float *host, long long n) {
+  if (!f || !host || n != f->off.total) return LBM_EINVAL;
+  FTRY(f, cudaMemcpyAsync(f->p, host, n * 4, cudaMemcpyHostToDevice, f->stream));
+  int rc = refresh_weights(f);
+  if (rc) return rc;
+  FTRY(f, cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+int lbm_fno_get_params(const lbm_fno *f, float *host, long long n) {
+  if (!f || !host || n != f->off.total) return LBM_EINVAL;
+  if (cudaMemcpyAsync(host, f->p, n * 4, cudaMemcpyDeviceToHost, f->stream) != cudaSuccess ||
+      cudaStreamSynchronize(f->stream) != cudaSuccess)
+    return LBM_ECUDA;
+  return LBM_OK;
+}
+
+int lbm_fno_get_grads(const lbm_fno *f, float *host, long long n) {
+  if (!f || !host || n != f->off.total) return LBM_EINVAL;
+  if (cudaMemcpyAsync(host, f->g, n * 4, cudaMemcpyDeviceToHost, f->stream) != cudaSuccess ||
+      cudaStreamSynchronize(f->stream) != cudaSuccess)
+    return LBM_ECUDA;
+  return LBM_OK;
+}
+
+int lbm_fno_zero_grads(lbm_fno *f) {
+  if (!f) return LBM_EINVAL;
+  FTRY(f, cudaMemsetAsync(f->g, 0, f->off.total * 4, f->stream));
+  return LBM_OK;
+}
+
+int lbm_fno_set_norm(lbm_fno *f, const float mean[6], const float std_in[6], const float std_out[6]) {
+  if (!f || !mean || !std_in || !std_out) return LBM_EINVAL;
+  for (int c = 0; c < 6; c++) {
+    if (!(std_in[c] > 0.0f) || !(std_out[c] > 0.0f)) return ferr(f, LBM_EINVAL, "non-positive scale");
+    f->norm_mean[c] = mean[c];
+    f->norm_std[c] = std_in[c];
+    f->out_std[c] = std_out[c];
+  }
+  return LBM_OK;
+}
+
+static Norm norm_of(const lbm_fno *f) {
+  Norm nm;
+  for (int c = 0; c < 6; c++) {
+    nm.mean[c] = f->norm_mean[c];
+    nm.std_in[c] = f->norm_std[c];
+    nm.std_out[c] = f->out_std[c];
+  }
+  return nm;
+}
+
+int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double *loss) {
+  if (!f || !now || !next) return LBM_EINVAL;
+  const long long P = f->P;
+  const Norm nm = norm_of(f);
+  k_pack_state<<<nblk((long long)f->cin * P), 256, 0, f->stream>>>(now, f->x16, f->cin, P, nm);
+  k_pack_target<<<nblk((long long)f->cout * P), 256, 0, f->stream>>>(now, next, f->tgt, f->cout, P, nm);
+  f->launches += 2;
+  int rc = forward(f);
+  if (rc) return rc;
+  return backward(f, loss);
+}
+
+int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, float grad_scale) {
+  if (!f || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return LBM_EINVAL;
+  f->adam_t++;
+  const double t = (double)f->adam_t;
+  const float lr_t = (float)(lr * sqrt(1.0 - pow((double)beta2, t)) / (1.0 - pow((double)beta1, t)));
+  fno::k_adam<<<nblk(f->off.total), 256, 0, f->stream>>>(f->p, f->g, f->m, f->v, f->off.total, lr_t, beta1, beta2, eps,
+                                                         grad_scale);
+  f->launches++;
+  FTRY(f, cudaGetLastError());
+  FTRY(f, cudaMemsetAsync(f->g, 0, f->off.total * 4, f->stream));
+  return refresh_weights(f);
+}
+
+// FP64 sum of n values (fixed-order two-level reduction), synchronises
+static int dsum(lbm_fno *f, const double *a, long long n, double *out) {
+  const int blocks = 1024;
+  k_sum<<<blocks, 256, 0, f->stream>>>(a, n, f->red);
+  f->launches++;
+  FTRY(f, cudaMemcpyAsync(f->h_red, f->red, blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  FTRY(f, cudaStreamSynchronize(f->stream));
+  double s = 0.0;
+  for (int i = 0; i < blocks; i++) s += f->h_red[i];
+  *out = s;
+  return LBM_OK;
+}
+
+int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok) {
+  if (!f || !now || !next || now == next) return LBM_EINVAL;
+  const long long P = f->P;
+  const Norm nm = norm_of(f);
+  k_pack_state<<<nblk((long long)f->cin * P), 256, 0, f->stream>>>(now, f->x16, f->cin, P, nm);
+  f->launches++;
+  int rc = forward(f);
+  if (rc) return rc;
+  k_unpack<<<nblk(6 * P), 256, 0, f->stream>>>(now, f->y, next, P, nm);
+  f->launches++;
+  FTRY(f, cudaGetLastError());
+  // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g
+  double g0 = 0, g1 = 0;
+  rc = dsum(f, now, P, &g0);
+  if (!rc) rc = dsum(f, next, P, &g1);
+  if (rc) return rc;
+  const double dg = fabs(g1 - g0) / fmax(g0, 1e-300), dl = fabs(g1 - g0) / fmax((double)P - g0, 1e-300);
+  const double d = isfinite(g1) ? fmax(dg, dl) : INFINITY;
+  if (drift) *drift = d;
+  if (ok) *ok = d <= max_drift;
+  return LBM_OK;
+}
+
+int lbm_fno_launch_count(const lbm_fno *f, long long *n) {
+  if (!f || !n) return LBM_EINVAL;
+  *n = f->launches;
+  return LBM_OK;
+}
+
+const char *lbm_fno_last_error(const lbm_fno *f) { return f ? f->err : ""; }
+
+int lbm_fno_gemm(int ta, int tb, int M, int N, int K, float alpha, const void *A, int lda, long long sA,
+                 const void *B, int ldb, long long sB, float beta, void *C, int ldc, long long sC, int batch,
+                 int out_f32, int ksplit, void *stream) {
+  if (!A || !B || !C) return LBM_EINVAL;
+  G g;
+  g.A = (const bf16 *)A; g.B = (const bf16 *)B; g.C = C;
+  g.M = M; g.N = N; g.K = K; g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.sA = sA; g.sB = sB; g.sC = sC;
+  g.batch = batch; g.alpha = alpha; g.beta = beta; g.ta = ta != 0; g.tb = tb != 0; g.out_f32 = out_f32 != 0;
+  g.ksplit = ksplit;
+  if (ksplit > 1 && beta != 1.0f) return LBM_EINVAL;
+  cudaError_t e = gemm(g, (cudaStream_t)stream);
+  return e == cudaSuccess ? LBM_OK : (e == cudaErrorInvalidValue || e == cudaErrorMisalignedAddress ? LBM_EINVAL : LBM_ECUDA);
+}
+
+}  // extern "C"
