@@ -14,8 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Simulation", "Batch", "LBMError", "load_library", "lattice_tables", "tile_limit", "PRECISION", "LATTICE",
-           "BC"]
+__all__ = ["Simulation", "Batch", "Surrogate", "LBMError", "load_library", "lattice_tables", "tile_limit", "fno_gemm",
+           "PRECISION", "LATTICE", "BC"]
 
 LATTICE = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "fp64dev": 3}
@@ -82,6 +82,23 @@ def load_library(build_if_missing=True):
             "lbm_set_tile": (I, [P, I, I, I]),
             "lbm_get_tile": (I, [P, ctypes.POINTER(I)]),
             "lbm_tile_limit": (I, [I, I, ctypes.POINTER(I)]),
+            "lbm_fno_create": (I, [I, I, I, I, I, ctypes.POINTER(P)]),
+            "lbm_fno_num_params": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_fno_set_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+            "lbm_fno_get_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+            "lbm_fno_get_grads": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+            "lbm_fno_zero_grads": (I, [P]),
+            "lbm_fno_set_norm": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_float)]),
+            "lbm_fno_set_stream": (I, [P, P]),
+            "lbm_fno_accumulate": (I, [P, dp, dp, ctypes.POINTER(D)]),
+            "lbm_fno_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "lbm_fno_advance": (I, [P, dp, dp, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
+            "lbm_fno_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_fno_last_error": (ctypes.c_char_p, [P]),
+            "lbm_fno_destroy": (I, [P]),
+            "lbm_fno_gemm": (I, [I, I, I, I, I, ctypes.c_float, dp, I, ctypes.c_longlong, dp, I, ctypes.c_longlong,
+                                 ctypes.c_float, dp, I, ctypes.c_longlong, I, I, I, P]),
             "lbm_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_last_error": (ctypes.c_char_p, [P]),
             "lbm_destroy": (I, [P]),
@@ -399,3 +416,126 @@ class Simulation:
         out = (ctypes.c_double * 8)()
         self._check(self._lib.lbm_get_diag(self._h, out), "lbm_get_diag")
         return np.array(out[:])
+
+
+def _f32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Surrogate:
+    """The learned 2D surrogate (include/lbm.h, lbm_fno_*): a factorised
+    Fourier neural operator over an nx x ny D2Q9 state.  States are torch
+    float64 CUDA tensors of shape (6, nx*ny): alpha_g, u_g (x, y), u_l (x, y),
+    p_k."""
+
+    def __init__(self, nx, ny, channels=64, modes=32, layers=4):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self._lib.lbm_fno_create(int(nx), int(ny), int(channels), int(modes), int(layers), ctypes.byref(h))
+        if rc:
+            raise LBMError(rc, "lbm_fno_create(%d, %d, %d, %d, %d)" % (nx, ny, channels, modes, layers))
+        self._h = h
+        self.nx, self.ny, self.channels, self.modes, self.layers = nx, ny, channels, modes, layers
+        n = ctypes.c_longlong()
+        self._lib.lbm_fno_num_params(h, ctypes.byref(n))
+        self.num_params = n.value
+
+    def _check(self, rc, what):
+        if rc:
+            msg = self._lib.lbm_fno_last_error(self._h)
+            raise LBMError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def set_stream(self, stream):
+        self._check(self._lib.lbm_fno_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "lbm_fno_set_stream")
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError("expected %d parameters" % self.num_params)
+        self._check(self._lib.lbm_fno_set_params(self._h, _f32p(p), p.size), "lbm_fno_set_params")
+
+    def params(self):
+        p = np.empty(self.num_params, np.float32)
+        self._check(self._lib.lbm_fno_get_params(self._h, _f32p(p), p.size), "lbm_fno_get_params")
+        return p
+
+    def grads(self):
+        g = np.empty(self.num_params, np.float32)
+        self._check(self._lib.lbm_fno_get_grads(self._h, _f32p(g), g.size), "lbm_fno_get_grads")
+        return g
+
+    def zero_grads(self):
+        self._check(self._lib.lbm_fno_zero_grads(self._h), "lbm_fno_zero_grads")
+
+    def set_norm(self, mean, std_in, std_out):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (mean, std_in, std_out)]
+        self._norm = a
+        self._check(self._lib.lbm_fno_set_norm(self._h, *[_f32p(v) for v in a]), "lbm_fno_set_norm")
+
+    @staticmethod
+    def _state(t):
+        if not (_is_torch(t) and t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+            raise ValueError("states are contiguous float64 CUDA tensors of shape (6, nx*ny)")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def accumulate(self, now, nxt):
+        loss = ctypes.c_double()
+        self._check(self._lib.lbm_fno_accumulate(self._h, self._state(now), self._state(nxt), ctypes.byref(loss)),
+                    "lbm_fno_accumulate")
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
+        self._check(self._lib.lbm_fno_adam(self._h, float(lr), float(beta1), float(beta2), float(eps),
+                                           float(grad_scale)), "lbm_fno_adam")
+
+    def advance(self, now, out, max_drift=1e-4):
+        """out = surrogate(now); returns (drift, ok)."""
+        d = ctypes.c_double()
+        ok = ctypes.c_int()
+        self._check(self._lib.lbm_fno_advance(self._h, self._state(now), self._state(out), float(max_drift),
+                                              ctypes.byref(d), ctypes.byref(ok)), "lbm_fno_advance")
+        return d.value, bool(ok.value)
+
+    @property
+    def launches(self):
+        n = ctypes.c_longlong()
+        self._lib.lbm_fno_launch_count(self._h, ctypes.byref(n))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fno_gemm(A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0, batch=1, sA=0, sB=0, sC=0, ksplit=1, M=None,
+             N=None, K=None, lda=None, ldb=None, ldc=None, stream=None):
+    """The surrogate's BF16 matrix product (lbm_fno_gemm) on torch CUDA
+    tensors: A, B bfloat16, C float32 or bfloat16 (2D row-major, or 3D with
+    the batch first)."""
+    lib = load_library()
+    a2, b2, c2 = (t if t.dim() == 2 else t[0] for t in (A, B, C))
+    M = M if M is not None else c2.shape[0]
+    N = N if N is not None else c2.shape[1]
+    K = K if K is not None else (a2.shape[0] if ta else a2.shape[1])
+    lda = lda if lda is not None else a2.stride(0)
+    ldb = ldb if ldb is not None else b2.stride(0)
+    ldc = ldc if ldc is not None else c2.stride(0)
+    if batch > 1:
+        sA = sA or (A.stride(0) if A.dim() == 3 else 0)
+        sB = sB or (B.stride(0) if B.dim() == 3 else 0)
+        sC = sC or (C.stride(0) if C.dim() == 3 else 0)
+    import torch
+    out_f32 = 1 if C.dtype == torch.float32 else 0
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    rc = lib.lbm_fno_gemm(int(ta), int(tb), M, N, K, float(alpha), ctypes.c_void_p(A.data_ptr()), lda, sA,
+                          ctypes.c_void_p(B.data_ptr()), ldb, sB, float(beta), ctypes.c_void_p(C.data_ptr()), ldc, sC,
+                          batch, out_f32, int(ksplit), st)
+    if rc:
+        raise LBMError(rc, "lbm_fno_gemm")

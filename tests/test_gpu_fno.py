@@ -1,0 +1,155 @@
+"""GPU parity of the learned surrogate (lbm_fno_*) against the FP64 reference.
+
+- The BF16 matrix product (lbm_fno_gemm), every transpose combination, FP32
+  and BF16 outputs, batch strides, split-K, ragged sizes (multiples of 16),
+  against float64 products of the same BF16-rounded inputs: FP32 output
+  within 1e-5 relative (FP32 accumulation), BF16 output within 1e-2.
+- The surrogate step (lbm_fno_advance) against oracle/fno_ref.advance, the
+  loss and the parameter gradient (lbm_fno_accumulate) against
+  oracle/fno_ref.loss_and_grad (float64, FFT-based, autodiff pinned to finite
+  differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2).  The
+  kernels round weights and activations to BF16 (8 significant bits), so the
+  bars are relative L2 3e-2 on the state increment and the gradient of every
+  parameter block, 2e-2 on the loss.
+- One Adam step against the textbook update of the gradients the library
+  returned; the mass-drift test of the fallback against the drift recomputed
+  from the returned state.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2409_10399_gb300 as lbm
+from oracle import fno_ref
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (32, 48, 16, 8, 2)  # nx, ny, C, K, L
+
+
+def _bf(t):
+    return t.to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("out", ["f32", "bf16"])
+def test_gemm_against_float64(ta, tb, out):
+    g = torch.Generator(device="cpu").manual_seed(7)
+    M, N, K, batch = 48, 80, 96, 3
+    A = _bf(torch.randn((batch, K, M) if ta else (batch, M, K), generator=g)).cuda()
+    B = _bf(torch.randn((batch, N, K) if tb else (batch, K, N), generator=g)).cuda()
+    C0 = torch.randn((batch, M, N), generator=g)
+    C = C0.to(torch.float32 if out == "f32" else torch.bfloat16).cuda()
+    lbm.fno_gemm(A, B, C, ta=ta, tb=tb, alpha=0.5, beta=0.25, batch=batch, M=M, N=N, K=K)
+    torch.cuda.synchronize()
+    a = A.double().cpu()
+    b = B.double().cpu()
+    ref = 0.5 * torch.matmul(a.transpose(1, 2) if ta else a, b.transpose(1, 2) if tb else b) + \
+        0.25 * C0.to(C.dtype).double()
+    err = (C.double().cpu() - ref).norm() / ref.norm()
+    assert err < (1e-5 if out == "f32" else 1e-2), err
+
+
+def test_gemm_split_k_and_strided_rows():
+    g = torch.Generator(device="cpu").manual_seed(8)
+    M, N, K = 32, 64, 4096
+    A = _bf(torch.randn((M, K), generator=g)).cuda()
+    Bfull = _bf(torch.randn((N, K + 64), generator=g)).cuda()   # ldb > K
+    C0 = torch.randn((M, N), generator=g).float().cuda()
+    C = C0.clone()
+    lbm.fno_gemm(A, Bfull, C, tb=True, beta=1.0, ksplit=7, M=M, N=N, K=K, ldb=K + 64)
+    torch.cuda.synchronize()
+    ref = A.double() @ Bfull[:, :K].double().T + C0.double()
+    assert ((C.double() - ref).norm() / ref.norm()).item() < 1e-5
+    with pytest.raises(lbm.LBMError):
+        lbm.fno_gemm(A, Bfull, C, tb=True, beta=0.0, ksplit=7, M=M, N=N, K=K, ldb=K + 64)  # split needs beta = 1
+    with pytest.raises(lbm.LBMError):
+        lbm.fno_gemm(A, Bfull, C, tb=True, M=M, N=N, K=40, ldb=K + 64)                     # K not a multiple of 16
+
+
+def _case(seed=11, scale=0.5):
+    nx, ny, C, K, L = DIMS
+    r = np.random.default_rng(seed)
+    n = sum(int(np.prod(s)) for _, s in fno_ref.layout(C, K, L))
+    p = (r.standard_normal(n) * scale / np.sqrt(C)).astype(np.float32)
+    P = nx * ny
+    x = (np.arange(P) % nx) / nx
+    y = (np.arange(P) // nx) / ny
+    norm = (np.array([0.3, 0, 0, 0, 0, 1 / 3]), np.array([0.1, 1e-3, 1e-3, 5e-4, 5e-4, 1e-6]),
+            np.array([1e-3, 1e-4, 1e-4, 5e-5, 5e-5, 1e-7]))
+    now = np.stack([0.3 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+                    1e-3 * np.sin(2 * np.pi * y), 1e-3 * np.cos(2 * np.pi * x),
+                    -5e-4 * np.sin(2 * np.pi * y), 2e-4 * np.cos(2 * np.pi * x),
+                    1 / 3 + 1e-6 * np.sin(2 * np.pi * (x + y))])
+    now = now + 0.1 * norm[1][:, None] * r.standard_normal((6, P))
+    nxt = now + norm[2][:, None] * r.standard_normal((6, P))
+    return p, now, nxt, norm
+
+
+def _model(p, norm):
+    nx, ny, C, K, L = DIMS
+    m = lbm.Surrogate(nx, ny, C, K, L)
+    m.set_params(p)
+    m.set_norm(*norm)
+    return m
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_advance_against_reference():
+    p, now, _, norm = _case()
+    m = _model(p, norm)
+    now_d = torch.from_numpy(now).cuda().contiguous()
+    out = torch.empty_like(now_d)
+    drift, ok = m.advance(now_d, out, max_drift=1.0)
+    got = out.cpu().numpy()
+    ref = fno_ref.advance(p.astype(np.float64), now, DIMS, norm)
+    for c in range(6):
+        assert _rel(got[c] - now[c], ref[c] - now[c]) < 3e-2, c
+    s0, s1 = now[0].sum(), got[0].sum()
+    expect = max(abs(s1 - s0) / s0, abs(s1 - s0) / (now.shape[1] - s0))
+    assert abs(drift - expect) <= 1e-9 * max(expect, 1e-30) + 1e-15
+    assert ok == (expect <= 1.0)
+    _, ok0 = m.advance(now_d, out, max_drift=0.0)
+    assert not ok0  # any change of sum(alpha_g) fails a zero tolerance
+
+
+def test_loss_and_gradient_against_reference():
+    p, now, nxt, norm = _case(seed=12)
+    m = _model(p, norm)
+    m.zero_grads()
+    loss = m.accumulate(torch.from_numpy(now).cuda().contiguous(), torch.from_numpy(nxt).cuda().contiguous())
+    g = m.grads()
+    ref_loss, ref_g = fno_ref.loss_and_grad(p.astype(np.float64), now, nxt, DIMS, norm)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
+    nx, ny, C, K, L = DIMS
+    at = 0
+    for name, shape in fno_ref.layout(C, K, L):
+        n = int(np.prod(shape))
+        a, b = g[at:at + n], ref_g[at:at + n]
+        at += n
+        if np.linalg.norm(b) == 0.0:
+            continue
+        if name.startswith("B") and name[1] in "xy":
+            # mode 0 of B_k has no effect (sin 0 = 0): its gradient is zero on both sides
+            b0, a0 = b.reshape(shape)[0], a.reshape(shape)[0]
+            assert np.abs(a0).max() <= 1e-6 * np.abs(b).max() + 1e-30 and np.abs(b0).max() < 1e-9 * np.abs(b).max()
+        assert _rel(a, b) < 3e-2, (name, _rel(a, b))
+
+
+def test_adam_step_is_the_textbook_update():
+    p, now, nxt, norm = _case(seed=13)
+    m = _model(p, norm)
+    m.zero_grads()
+    m.accumulate(torch.from_numpy(now).cuda().contiguous(), torch.from_numpy(nxt).cuda().contiguous())
+    g = m.grads().astype(np.float64) * 0.5
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    m.adam(lr, b1, b2, eps, grad_scale=0.5)
+    mt, vt = (1 - b1) * g, (1 - b2) * g * g
+    ref = p - lr * np.sqrt(1 - b2) / (1 - b1) * mt / (np.sqrt(vt) + eps)
+    got = m.params()
+    assert np.allclose(got, ref, rtol=1e-5, atol=1e-7)
+    assert np.abs(m.grads()).max() == 0.0  # zeroed after the step
