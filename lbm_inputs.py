@@ -48,6 +48,13 @@ WORKLOADS = {
                      inlet_lo=192, inlet_hi=320, in_alpha=(0.01, 0.3), in_ug=(4.3e-4, 4.3e-3),
                      in_ul=(0.0, 0.0), inlet_ul_mode=1, ramp_nt=1667),
     ),
+    # surrogate workload: closed 2D box (periodic x, walls y), D2Q9 FP32, gas
+    # plumes at random places (fields_plumes), R = 1000, snapshots every 64 steps
+    "surrogate2d": dict(
+        lattice="D2Q9", dims=(256, 1024, 1), steps=4096, precision="fp32",
+        physics=dict(_common_physics(), wall_friction=False, g_axis=1,
+                     bc_lo=(PERIODIC, WALL, 0), bc_hi=(PERIODIC, WALL, 0)),
+    ),
     # batched sweep: 256 independent D2Q9 columns (see batch_sweep), FP32
     "batch256": dict(lattice="D2Q9", dims=None, steps=10000, precision="fp32", physics=None),
     # 3D column, D3Q19, walls on the four x/y faces, periodic z, gravity along z.
@@ -113,6 +120,25 @@ def fields_smooth2d(n, eps, U=0.64):
     u = eps * U * np.stack([np.sin(2.0 * np.pi * x) * np.cos(2.0 * np.pi * y),
                             -np.cos(2.0 * np.pi * x) * np.sin(2.0 * np.pi * y)]).reshape(2, -1)
     return dict(alpha_g=a, u_g=u.copy(), u_l=u.copy(), p_k=np.full(n * n, CS2_PK))
+
+
+def fields_plumes(nx, ny, seed, background=0.02, blobs=(3, 7), amp=(0.15, 0.4), radius=(8.0, 24.0)):
+    """Gas plumes in a liquid column: alpha_g = background plus Gaussian blobs
+    (count uniform in `blobs`, amplitude in `amp`, radius in `radius` nodes)
+    centred at random x and in the lower half of y, clipped to [0.01, 0.6];
+    both phases at rest plus U(-1e-5, 1e-5) velocity noise; p_k reference."""
+    r = rng(seed)
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    a = np.full((ny, nx), background)
+    for _ in range(int(r.integers(blobs[0], blobs[1] + 1))):
+        xc, yc = r.uniform(0, nx), r.uniform(0.1 * ny, 0.5 * ny)
+        rad, am = r.uniform(*radius), r.uniform(*amp)
+        dx = np.minimum(np.abs(x - xc), nx - np.abs(x - xc))  # periodic in x
+        a = a + am * np.exp(-(dx ** 2 + (y - yc) ** 2) / (2.0 * rad ** 2))
+    n = nx * ny
+    return dict(alpha_g=np.clip(a, 0.01, 0.6).reshape(-1), u_g=r.uniform(-1e-5, 1e-5, (2, n)),
+                u_l=r.uniform(-1e-5, 1e-5, (2, n)), p_k=np.full(n, CS2_PK))
 
 
 def rng(seed):

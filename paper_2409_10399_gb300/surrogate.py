@@ -1,0 +1,263 @@
+"""Learned surrogate workload: a ~2.1 M-parameter factorised Fourier neural
+operator (lbm_fno_*) trained on trajectories of the library's own 2D LBM, that
+advances the state by 64 LBM steps per call, with the LBM as fallback.
+
+    python -m paper_2409_10399_gb300.surrogate [--train 32] [--test 4] [--epochs 12]
+
+Workload (lbm_inputs "surrogate2d"): D2Q9 256 x 1024, FP32, R = 1000, the
+box2d physics in a closed box (periodic x, walls y), so that the per-phase
+volumes sum(alpha_g), sum(alpha_l) are conserved and the surrogate's mass
+check means something; initial states are gas plumes at random places
+(lbm_inputs.fields_plumes, seed per trajectory).  Each trajectory runs 4,096
+steps with a snapshot every 64: 64 (state, state 64 steps later) pairs.
+
+Training: one sample per forward/backward (lbm_fno_accumulate), gradients
+averaged over a batch of samples, Adam with a cosine-decayed learning rate.
+Evaluation on held-out trajectories, per 64-step window and over rollouts of
+chained surrogate calls: relative L2 error of the predicted increment against
+the LBM's increment for each channel, of the state, the persistence baseline
+(next = now) for context, and the fallback rate (per-phase volume drift above
+1e-4 -> the window is advanced with the LBM instead).  Speed: device time of
+one surrogate call against 64 LBM steps (FP32) of the same state.
+One JSON line per result.
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+import lbm_inputs
+from . import Simulation, Surrogate
+from . import params as lparams
+
+WINDOW = 64
+CH = ("alpha_g", "u_gx", "u_gy", "u_lx", "u_ly", "p_k")
+
+
+def _lbm_params(precision="fp32"):
+    w = lbm_inputs.WORKLOADS["surrogate2d"]
+    return lparams.lattice_params(w["physics"], precision=precision)
+
+
+def _views(buf):
+    """alpha_g, u_g, u_l, p_k views of a (6, N) state tensor (lbm_get_moments layout)."""
+    return dict(alpha_g=buf[0], u_g=buf[1:3], u_l=buf[3:5], p_k=buf[5])
+
+
+def trajectories(n, seed0, nx, ny, steps):
+    """(n, steps / 64 + 1, 6, nx*ny) float64 CUDA tensor of snapshots."""
+    import torch
+    P = nx * ny
+    nsnap = steps // WINDOW + 1
+    out = torch.empty((n, nsnap, 6, P), dtype=torch.float64, device="cuda")
+    p = _lbm_params()
+    for i in range(n):
+        s = Simulation("D2Q9", (nx, ny, 1), p)
+        s.set_stream(torch.cuda.current_stream())
+        s.init(**lbm_inputs.fields_plumes(nx, ny, seed0 + i))
+        for k in range(nsnap):
+            if k:
+                s.step(WINDOW)
+            s.moments(out=_views(out[i, k]))
+        s.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def fit_norm(data):
+    """Per-channel mean and std of the states and std of the 64-step increments."""
+    x = data[:, :-1]
+    d = data[:, 1:] - data[:, :-1]
+    mean = x.mean(dim=(0, 1, 3)).cpu().numpy()
+    std = x.std(dim=(0, 1, 3)).cpu().numpy()
+    dstd = d.std(dim=(0, 1, 3)).cpu().numpy()
+    tiny = np.array([1e-12, 1e-15, 1e-15, 1e-15, 1e-15, 1e-18])
+    return mean, np.maximum(std, tiny), np.maximum(dstd, tiny)
+
+
+def _layout(C, K, L):
+    """Parameter blocks in the library's order (include/lbm.h, lbm_fno_set_params)."""
+    out = [("W_in", (C, 16)), ("b_in", (C,))]
+    for l in range(L):
+        out += [("W%d" % l, (C, C)), ("b%d" % l, (C,)), ("Ax%d" % l, (K, C, C)), ("Bx%d" % l, (K, C, C)),
+                ("Ay%d" % l, (K, C, C)), ("By%d" % l, (K, C, C))]
+    out += [("W_out", (16, C)), ("b_out", (16,))]
+    return out
+
+
+def init_params(C, K, L, seed=0):
+    """Seeded initial weights: pointwise W ~ N(0, 1/fan_in), spectral A, B ~
+    N(0, 1/(2 C K)) (the 2K coefficients of a mode sum back into one value),
+    biases zero, the output layer scaled down so that the first predictions
+    are near the persistence baseline."""
+    r = np.random.default_rng(seed)
+    parts = []
+    for name, shape in _layout(C, K, L):
+        if name.startswith("b"):
+            parts.append(np.zeros(shape))
+        elif name[0] in "AB":
+            parts.append(r.standard_normal(shape) / math.sqrt(2.0 * C * K))
+        elif name == "W_out":
+            parts.append(0.1 * r.standard_normal(shape) / math.sqrt(C))
+        else:
+            parts.append(r.standard_normal(shape) / math.sqrt(shape[1]))
+    return np.concatenate([x.reshape(-1) for x in parts]).astype(np.float32)
+
+
+def train(model, data, epochs, batch=8, lr=2e-3, seed=0, log=None):
+    """Adam over all (trajectory, window) pairs of `data`, shuffled per epoch,
+    cosine learning-rate decay; returns the mean loss of each epoch."""
+    n, nsnap = data.shape[0], data.shape[1]
+    pairs = [(i, k) for i in range(n) for k in range(nsnap - 1)]
+    r = np.random.default_rng(seed)
+    steps_total = epochs * math.ceil(len(pairs) / batch)
+    step = 0
+    hist = []
+    for ep in range(epochs):
+        order = r.permutation(len(pairs))
+        tot, cnt = 0.0, 0
+        for b0 in range(0, len(order), batch):
+            idx = order[b0:b0 + batch]
+            for j in idx:
+                i, k = pairs[j]
+                tot += model.accumulate(data[i, k], data[i, k + 1])
+                cnt += 1
+            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps_total))
+            model.adam(lr_t, grad_scale=1.0 / len(idx))
+            step += 1
+        hist.append(tot / cnt)
+        if log:
+            log(dict(epoch=ep, loss=hist[-1]))
+    return hist
+
+
+def _rel(a, b):
+    nb = float(b.norm())
+    return float((a - b).norm()) / nb if nb > 0 else float(a.norm())
+
+
+def evaluate(model, data, max_drift=1e-4, rollout=8):
+    """Per-window and rollout errors on held-out trajectories."""
+    import torch
+    n, nsnap = data.shape[0], data.shape[1]
+    out = torch.empty_like(data[0, 0])
+    inc = {c: [] for c in CH}
+    state_err, persist_err, drifts, fallbacks = [], [], [], 0
+    for i in range(n):
+        for k in range(nsnap - 1):
+            now, ref = data[i, k], data[i, k + 1]
+            d, ok = model.advance(now, out, max_drift=max_drift)
+            drifts.append(d)
+            fallbacks += 0 if ok else 1
+            for c, name in enumerate(CH):
+                inc[name].append(_rel(out[c] - now[c], ref[c] - now[c]))
+            state_err.append(_rel(out[:5], ref[:5]))
+            persist_err.append(_rel(now[:5], ref[:5]))
+    # rollouts: chained surrogate calls from snapshot 0 against the LBM
+    roll = []
+    cur = data[:, 0].clone()
+    nxt = torch.empty_like(cur[0])
+    for k in range(1, min(rollout, nsnap - 1) + 1):
+        errs = []
+        for i in range(n):
+            model.advance(cur[i], nxt, max_drift=1e30)
+            cur[i].copy_(nxt)
+            errs.append(_rel(cur[i][0], data[i, k][0]))
+        roll.append(float(np.mean(errs)))
+    return dict(windows=n * (nsnap - 1),
+                increment_rel_l2={c: float(np.median(v)) for c, v in inc.items()},
+                state_rel_l2=float(np.median(state_err)), persistence_rel_l2=float(np.median(persist_err)),
+                drift_median=float(np.median(drifts)), drift_max=float(np.max(drifts)),
+                fallback_rate=fallbacks / max(1, len(drifts)), rollout_alpha_rel_l2=roll)
+
+
+def advance_with_fallback(model, sim, now, out, max_drift=1e-4):
+    """One 64-step window: the surrogate, or the LBM when the volume check fails."""
+    d, ok = model.advance(now, out, max_drift=max_drift)
+    if not ok:
+        sim.init(**_views(now))
+        sim.step(WINDOW)
+        sim.moments(out=_views(out))
+    return ok, d
+
+
+def speed(model, state, nx, ny, reps=20):
+    """Device time of a surrogate call and of 64 LBM steps on the same state."""
+    import torch
+    out = torch.empty_like(state)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    model.advance(state, out, max_drift=1e30)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        model.advance(state, out, max_drift=1e30)
+    e1.record()
+    torch.cuda.synchronize()
+    t_sur = e0.elapsed_time(e1) / reps
+    s = Simulation("D2Q9", (nx, ny, 1), _lbm_params())
+    s.set_stream(torch.cuda.current_stream())
+    s.init(**_views(state))
+    s.step(WINDOW)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        s.step(WINDOW)
+    e1.record()
+    torch.cuda.synchronize()
+    t_lbm = e0.elapsed_time(e1) / reps
+    s.close()
+    flops = model_flops(model.nx, model.ny, model.channels, model.modes, model.layers)
+    return dict(surrogate_ms=t_sur, lbm_64_steps_ms=t_lbm, speedup=t_lbm / t_sur,
+                surrogate_tflops=flops / (t_sur * 1e-3) / 1e12, flops_per_call=flops)
+
+
+def model_flops(nx, ny, C, K, L):
+    """Multiply-add count x 2 of one forward pass (the matrix products)."""
+    P, K2 = nx * ny, 2 * K
+    per_layer = 2 * C * C * P                                   # pointwise
+    per_layer += 2 * K2 * C * ny * nx * 2                       # x: to and from coefficients
+    per_layer += 2 * K * (2 * C) * (2 * C) * ny                 # x: mode mixing
+    per_layer += 2 * K2 * C * nx * ny * 2                       # y: to and from coefficients
+    per_layer += 2 * K * (2 * C) * (2 * C) * nx                 # y: mode mixing
+    return L * per_layer + 2 * 16 * C * P * 2                   # lifting and projection
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=256)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--train", type=int, default=32)
+    ap.add_argument("--test", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4096)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--channels", type=int, default=64)
+    ap.add_argument("--modes", type=int, default=32)
+    ap.add_argument("--layers", type=int, default=4)
+    args = ap.parse_args()
+    emit = lambda d: print(json.dumps(d), flush=True)
+    t0 = time.time()
+    train_data = trajectories(args.train, 1000, args.nx, args.ny, args.steps)
+    test_data = trajectories(args.test, 9000, args.nx, args.ny, args.steps)
+    emit(dict(stage="data", train_trajectories=args.train, test_trajectories=args.test,
+              pairs=args.train * (train_data.shape[1] - 1), wall_s=time.time() - t0))
+    m = Surrogate(args.nx, args.ny, args.channels, args.modes, args.layers)
+    m.set_stream(torch.cuda.current_stream())
+    m.set_params(init_params(args.channels, args.modes, args.layers))
+    mean, std, dstd = fit_norm(train_data)
+    m.set_norm(mean, std, dstd)
+    emit(dict(stage="model", params=m.num_params, norm_mean=mean.tolist(), norm_std=std.tolist(),
+              increment_std=dstd.tolist()))
+    t1 = time.time()
+    hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))
+    emit(dict(stage="trained", epochs=args.epochs, final_loss=hist[-1], wall_s=time.time() - t1))
+    emit(dict(stage="test", **evaluate(m, test_data)))
+    emit(dict(stage="speed", nodes=args.nx * args.ny, **speed(m, test_data[0, 0].contiguous(), args.nx, args.ny)))
+
+
+if __name__ == "__main__":
+    main()
