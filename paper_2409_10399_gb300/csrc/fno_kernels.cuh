@@ -22,6 +22,9 @@ typedef __nv_bfloat16 bf16;
 // ksplit > 1 splits K into chunks of kchunk (a multiple of 32) over blocks,
 // each adding alpha times its partial product into a float C with atomics
 // (C += alpha op(A) op(B); beta is not applied).
+// With bias != null (float C only) the epilogue also adds bias[b] (one value
+// per batch entry) to the result, stores it in C and GELU(result) as bf16 at
+// the same index of hout: the last product of a surrogate layer.
 struct GemmArgs {
   const bf16 *A, *B;
   void *C;
@@ -29,7 +32,11 @@ struct GemmArgs {
   long long sA, sB, sC;  // batch strides (elements)
   float alpha, beta;
   int ksplit, kchunk;
+  const float *bias;
+  bf16 *hout;
 };
+
+__device__ __forceinline__ float gelu(float z);
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
 
@@ -107,20 +114,57 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
       wmma::store_matrix_sync(&sC[wm + 16 * i][wn + 16 * j], acc[i][j], GBN + 4, wmma::mem_row_major);
   __syncthreads();
   OutT *C = reinterpret_cast<OutT *>(g.C) + (long long)b * g.sC;
-  for (int v = tid; v < GBM * GBN; v += 128) {
-    const int r = v / GBN, c = v % GBN;
-    const int gr = m0 + r, gc = n0 + c;
-    if (gr < g.M && gc < g.N) {
-      OutT *p = C + (long long)gr * g.ldc + gc;
-      if constexpr (std::is_same<OutT, float>::value) {
-        if (g.ksplit > 1) {
-          atomicAdd(p, g.alpha * sC[r][c]);
-          continue;
-        }
+  // epilogue in groups of 4 columns (N and ldc are multiples of 8): every read
+  // of the old C is issued before any write, so the reads overlap
+  constexpr int PER = GBM * GBN / 4 / 128;
+  if constexpr (std::is_same<OutT, float>::value) {
+    if (g.ksplit > 1) {
+      for (int v = tid; v < GBM * GBN; v += 128) {
+        const int r = v / GBN, c = v % GBN, gr = m0 + r, gc = n0 + c;
+        if (gr < g.M && gc < g.N) atomicAdd(C + (long long)gr * g.ldc + gc, g.alpha * sC[r][c]);
       }
-      float val = g.alpha * sC[r][c];
-      if (g.beta != 0.0f) val += g.beta * (float)(*p);
-      *p = (OutT)val;
+      return;
+    }
+  }
+  float4 old[PER];
+#pragma unroll
+  for (int j = 0; j < PER; j++) {
+    const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
+    old[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g.beta != 0.0f && gr < g.M && gc < g.N) {
+      const OutT *p = C + (long long)gr * g.ldc + gc;
+      if constexpr (std::is_same<OutT, float>::value) {
+        old[j] = *reinterpret_cast<const float4 *>(p);
+      } else {
+        const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+        const bf16 *hb = reinterpret_cast<const bf16 *>(&raw);
+        old[j] = make_float4((float)hb[0], (float)hb[1], (float)hb[2], (float)hb[3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PER; j++) {
+    const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
+    if (gr >= g.M || gc >= g.N) continue;
+    float o[4] = {g.alpha * sC[r][c] + g.beta * old[j].x, g.alpha * sC[r][c + 1] + g.beta * old[j].y,
+                  g.alpha * sC[r][c + 2] + g.beta * old[j].z, g.alpha * sC[r][c + 3] + g.beta * old[j].w};
+    OutT *p = C + (long long)gr * g.ldc + gc;
+    if constexpr (std::is_same<OutT, float>::value) {
+      if (g.bias) {
+        const float bb = g.bias[b];
+        bf16 hv[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          o[e] += bb;
+          hv[e] = __float2bfloat16(gelu(o[e]));
+        }
+        *reinterpret_cast<uint2 *>(g.hout + (long long)b * g.sC + (long long)gr * g.ldc + gc) =
+            *reinterpret_cast<const uint2 *>(hv);
+      }
+      *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      bf16 hv[4] = {__float2bfloat16(o[0]), __float2bfloat16(o[1]), __float2bfloat16(o[2]), __float2bfloat16(o[3])};
+      *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(hv);
     }
   }
 }
@@ -158,19 +202,22 @@ __global__ void k_act_back(const float *dh, const float *z, float *dz, bf16 *dz1
   dz16[i] = __float2bfloat16(v);
 }
 
-// db[c] += sum_p dz[c][p]: one block per channel, fixed-order tree reduction
+// db[c] += sum_p dz[c][p]: blocks (chunk, c), each reducing its chunk of the
+// channel in a tree and adding it atomically
 __global__ void k_bias_grad(const float *dz, float *db, long long P) {
   __shared__ float s[256];
-  const int c = blockIdx.x;
+  const int c = blockIdx.y;
+  const long long chunk = (P + gridDim.x - 1) / gridDim.x, p0 = blockIdx.x * chunk;
+  const long long p1 = p0 + chunk < P ? p0 + chunk : P;
   float acc = 0.0f;
-  for (long long p = threadIdx.x; p < P; p += blockDim.x) acc += dz[(long long)c * P + p];
+  for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += dz[(long long)c * P + p];
   s[threadIdx.x] = acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[c] += s[0];
+  if (threadIdx.x == 0) atomicAdd(db + c, s[0]);
 }
 
 // squared error of the first `cv` of C channels: d = 2 (y - t) / (cv P)

@@ -105,6 +105,8 @@ struct G {
   float alpha = 1.0f, beta = 0.0f;
   bool ta = false, tb = false, out_f32 = true;
   int ksplit = 1;  // > 1: K split over blocks, FP32 atomic accumulation (beta must be 1)
+  const float *bias = nullptr;  // fused epilogue: + bias[batch], GELU into hout
+  bf16 *hout = nullptr;
 };
 
 template <bool TA, bool TB, class OutT>
@@ -113,14 +115,18 @@ static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
-  if (g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1) return cudaErrorInvalidValue;
+  if (g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1 || g.sA % 8 ||
+      g.sB % 8 || g.sC % 8)
+    return cudaErrorInvalidValue;
+  if (g.bias && (!g.out_f32 || !g.hout || g.ksplit > 1 || ((uintptr_t)g.hout & 31))) return cudaErrorInvalidValue;
   if (((uintptr_t)g.A | (uintptr_t)g.B | (uintptr_t)g.C) & 31) return cudaErrorMisalignedAddress;
   if (g.ksplit > 1 && !g.out_f32) return cudaErrorInvalidValue;
   int ks = g.ksplit < 1 ? 1 : g.ksplit;
   int kchunk = ((g.K + ks - 1) / ks + fno::GBK - 1) / fno::GBK * fno::GBK;
   ks = (g.K + kchunk - 1) / kchunk;
   if ((long long)g.batch * ks > 65535) return cudaErrorInvalidValue;
-  fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk};
+  fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk,
+                  g.bias, g.hout};
   dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
   if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
   else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
@@ -228,8 +234,9 @@ static int spec_x(lbm_fno *f, const bf16 *h, bf16 *Hx, const bf16 *Wf, float *z)
   return LBM_OK;
 }
 
-// z += S^y(h); Hy is [2K][C][nx]
-static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z) {
+// z += S^y(h); Hy is [2K][C][nx].  The last product of the layer: it also adds
+// the bias and writes GELU(z) into hnext (fused epilogue).
+static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z, const float *bias, bf16 *hnext) {
   const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
   const long long P = f->P;
   G a;  // per channel c: Hy[:, c, :] (2K x nx) = B_y^T h[c]
@@ -249,6 +256,7 @@ static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z)
   c.B = f->O16; c.ldb = C * nx; c.sB = nx;
   c.C = z; c.ldc = nx; c.sC = P; c.beta = 1.0f;
   c.M = ny; c.N = nx; c.K = K2; c.batch = C;
+  c.bias = bias; c.hout = hnext;
   GTRY(f, c);
   return LBM_OK;
 }
@@ -273,10 +281,8 @@ static int forward(lbm_fno *f) {
     GTRY(f, w);
     int rc = spec_x(f, h, f->Hx16 + l * hx, f->Wfx16 + l * wf, z);
     if (rc) return rc;
-    rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z);
+    rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z, f->p + f->off.b[l], f->h16 + (l + 1) * CP);
     if (rc) return rc;
-    fno::k_bias_act<<<nblk(CP), 256, 0, f->stream>>>(z, f->p + f->off.b[l], f->h16 + (l + 1) * CP, C, P, 1);
-    f->launches++;
   }
   G o;  // y = W_out h_L (+ b_out)
   o.A = f->W_out16; o.lda = C; o.B = f->h16 + L * CP; o.ldb = (int)P; o.C = f->y; o.ldc = (int)P;
@@ -356,7 +362,7 @@ static int spec_y_back(lbm_fno *f, const bf16 *dz16, const bf16 *Hy, const bf16 
 
 // split of the long contractions over pixels (weight gradients)
 static int ksplit_for(long long K) {
-  const long long chunk = 4096;
+  const long long chunk = 512;
   long long s = (K + chunk - 1) / chunk;
   return (int)(s < 1 ? 1 : (s > 512 ? 512 : s));
 }
@@ -375,7 +381,7 @@ static int backward(lbm_fno *f, double *loss) {
   go.C = f->g + f->off.W_out; go.ldc = C; go.beta = 1.0f; go.ksplit = ksplit_for(P);
   go.M = f->cout; go.N = C; go.K = (int)P;
   GTRY(f, go);
-  fno::k_bias_grad<<<f->cout, 256, 0, f->stream>>>(f->dy, f->g + f->off.b_out, P);
+  fno::k_bias_grad<<<dim3(64, f->cout), 256, 0, f->stream>>>(f->dy, f->g + f->off.b_out, P);
   f->launches++;
   G gh;  // dh = W_out^T dy
   gh.A = f->W_out16; gh.ta = true; gh.lda = C; gh.B = f->dy16; gh.ldb = (int)P; gh.C = f->dh; gh.ldc = (int)P;
@@ -383,7 +389,7 @@ static int backward(lbm_fno *f, double *loss) {
   GTRY(f, gh);
   for (int l = L - 1; l >= 0; l--) {
     fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, f->z + l * CP, f->dz, f->dz16, CP, 1);
-    fno::k_bias_grad<<<C, 256, 0, f->stream>>>(f->dz, f->g + f->off.b[l], P);
+    fno::k_bias_grad<<<dim3(64, C), 256, 0, f->stream>>>(f->dz, f->g + f->off.b[l], P);
     f->launches += 2;
     const bf16 *h = f->h16 + l * CP;
     G gw;  // dW_l += dz h^T
@@ -404,7 +410,7 @@ static int backward(lbm_fno *f, double *loss) {
   }
   // lifting (no activation)
   fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, f->zin, f->dz, f->dz16, CP, 0);
-  fno::k_bias_grad<<<C, 256, 0, f->stream>>>(f->dz, f->g + f->off.b_in, P);
+  fno::k_bias_grad<<<dim3(64, C), 256, 0, f->stream>>>(f->dz, f->g + f->off.b_in, P);
   f->launches += 2;
   G gi;  // dW_in += dz x^T
   gi.A = f->dz16; gi.lda = (int)P; gi.B = f->x16; gi.tb = true; gi.ldb = (int)P;

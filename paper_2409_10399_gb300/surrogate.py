@@ -238,8 +238,16 @@ def main():
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--speed-only", action="store_true", help="time one surrogate call and 64 LBM steps, no training")
     args = ap.parse_args()
     emit = lambda d: print(json.dumps(d), flush=True)
+    if args.speed_only:
+        st = trajectories(1, 1000, args.nx, args.ny, WINDOW)[0, 1].contiguous()
+        m = Surrogate(args.nx, args.ny, args.channels, args.modes, args.layers)
+        m.set_stream(torch.cuda.current_stream())
+        m.set_params(init_params(args.channels, args.modes, args.layers))
+        emit(dict(stage="speed", nodes=args.nx * args.ny, **speed(m, st, args.nx, args.ny)))
+        return
     t0 = time.time()
     train_data = trajectories(args.train, 1000, args.nx, args.ny, args.steps)
     test_data = trajectories(args.test, 9000, args.nx, args.ny, args.steps)
