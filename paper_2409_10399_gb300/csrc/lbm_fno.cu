@@ -68,6 +68,7 @@ struct lbm_fno {
   bf16 *x16 = nullptr, *h16 = nullptr, *Hx16 = nullptr, *Hy16 = nullptr, *O16 = nullptr, *y16 = nullptr;
   float *z = nullptr, *zin = nullptr, *y = nullptr, *tgt = nullptr;
   float *dy = nullptr, *dh = nullptr, *dz = nullptr, *dWf = nullptr;
+  float *coef32 = nullptr;  // FP32 scratch of the split y-axis projections (2K x C x nx)
   bf16 *dy16 = nullptr, *dz16 = nullptr, *dO16 = nullptr, *dH16 = nullptr;
   double *part = nullptr, *h_part = nullptr, *red = nullptr, *h_red = nullptr;
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
@@ -234,17 +235,32 @@ static int spec_x(lbm_fno *f, const bf16 *h, bf16 *Hx, const bf16 *Wf, float *z)
   return LBM_OK;
 }
 
+// out[:, c, :] (2K x nx, layout [2K][C][nx], bf16) = basis^T x[c] for every
+// channel: a contraction over the ny nodes of a column, split over blocks
+// into the FP32 scratch (few output tiles, long K) and rounded once.
+static int project_y(lbm_fno *f, const bf16 *basis, const bf16 *x, bf16 *out) {
+  const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  const long long n = (long long)K2 * C * nx;
+  FTRY(f, cudaMemsetAsync(f->coef32, 0, n * sizeof(float), f->stream));
+  G a;
+  a.A = basis; a.ta = true; a.lda = K2;
+  a.B = x; a.ldb = nx; a.sB = f->P;
+  a.C = f->coef32; a.ldc = C * nx; a.sC = nx; a.beta = 1.0f;
+  a.M = K2; a.N = nx; a.K = ny; a.batch = C;
+  a.ksplit = ny >= 512 ? ny / 256 : 1;
+  GTRY(f, a);
+  fno::k_to_bf16<<<nblk(n), 256, 0, f->stream>>>(f->coef32, out, n);
+  f->launches++;
+  return LBM_OK;
+}
+
 // z += S^y(h); Hy is [2K][C][nx].  The last product of the layer: it also adds
 // the bias and writes GELU(z) into hnext (fused epilogue).
 static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z, const float *bias, bf16 *hnext) {
   const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
   const long long P = f->P;
-  G a;  // per channel c: Hy[:, c, :] (2K x nx) = B_y^T h[c]
-  a.A = f->By; a.ta = true; a.lda = K2;
-  a.B = h; a.ldb = nx; a.sB = P;
-  a.C = Hy; a.out_f32 = false; a.ldc = C * nx; a.sC = nx;
-  a.M = K2; a.N = nx; a.K = ny; a.batch = C;
-  GTRY(f, a);
+  int rc = project_y(f, f->By, h, Hy);  // Hy[:, c, :] (2K x nx) = B_y^T h[c]
+  if (rc) return rc;
   G b;  // per mode: O_k (2C x nx) = Wf_k H_k, rows (j C + c)
   b.A = Wf; b.lda = 2 * C; b.sA = 4LL * C * C;
   b.B = Hy; b.ldb = nx; b.sB = 2LL * C * nx;
@@ -331,12 +347,8 @@ static int spec_y_back(lbm_fno *f, const bf16 *dz16, const bf16 *Hy, const bf16 
                        float *gB) {
   const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
   const long long P = f->P;
-  G a;  // per channel: dO[:, c, :] = Byi^T dz[c]
-  a.A = f->Byi; a.ta = true; a.lda = K2;
-  a.B = dz16; a.ldb = nx; a.sB = P;
-  a.C = f->dO16; a.out_f32 = false; a.ldc = C * nx; a.sC = nx;
-  a.M = K2; a.N = nx; a.K = ny; a.batch = C;
-  GTRY(f, a);
+  int rc = project_y(f, f->Byi, dz16, f->dO16);  // dO[:, c, :] = Byi^T dz[c]
+  if (rc) return rc;
   G w;  // dWf_k = dO_k H_k^T
   w.A = f->dO16; w.lda = nx; w.sA = 2LL * C * nx;
   w.B = Hy; w.tb = true; w.ldb = nx; w.sB = 2LL * C * nx;
@@ -465,7 +477,7 @@ int lbm_fno_destroy(lbm_fno *f) {
   cudaStreamSynchronize(f->stream);
   void *bufs[] = {f->p, f->g, f->m, f->v, f->W_in16, f->W_out16, f->W16, f->Wfx16, f->Wfy16, f->Bx, f->Bxi, f->By,
                   f->Byi, f->x16, f->h16, f->Hx16, f->Hy16, f->O16, f->y16, f->z, f->zin, f->y, f->tgt, f->dy, f->dh,
-                  f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red};
+                  f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red, f->coef32};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (f->h_part) cudaFreeHost(f->h_part);
@@ -503,7 +515,8 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
       {(void **)&f->dh, CP * 4}, {(void **)&f->dz, CP * 4}, {(void **)&f->dWf, wf * 4},
       {(void **)&f->dy16, f->cout * P * 2}, {(void **)&f->dz16, CP * 2},
       {(void **)&f->dO16, hmax * 2}, {(void **)&f->dH16, hmax * 2},
-      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 2048 * 8}};
+      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 2048 * 8},
+      {(void **)&f->coef32, K2 * C * nx * 4}};
   for (auto &a : al) {
     if (cudaMalloc(a.p, (size_t)a.bytes) != cudaSuccess) {
       cudaGetLastError();

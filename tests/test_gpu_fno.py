@@ -7,7 +7,8 @@
 - The surrogate step (lbm_fno_advance) against oracle/fno_ref.advance, the
   loss and the parameter gradient (lbm_fno_accumulate) against
   oracle/fno_ref.loss_and_grad (float64, FFT-based, autodiff pinned to finite
-  differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2).  The
+  differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2) and a
+  tall one (32 x 512, L = 1) whose y-axis projections split over blocks.  The
   kernels round weights and activations to BF16 (8 significant bits), so the
   bars are relative L2 3e-2 on the state increment and the gradient of every
   parameter block, 2e-2 on the loss.
@@ -25,6 +26,7 @@ from oracle import fno_ref
 pytestmark = pytest.mark.gpu
 
 DIMS = (32, 48, 16, 8, 2)  # nx, ny, C, K, L
+TALL = (32, 512, 16, 8, 1)  # ny >= 512: the y-axis projections split over blocks
 
 
 def _bf(t):
@@ -68,8 +70,8 @@ def test_gemm_split_k_and_strided_rows():
         lbm.fno_gemm(A, Bfull, C, tb=True, M=M, N=N, K=40, ldb=K + 64)                     # K not a multiple of 16
 
 
-def _case(seed=11, scale=0.5):
-    nx, ny, C, K, L = DIMS
+def _case(seed=11, scale=0.5, dims=DIMS):
+    nx, ny, C, K, L = dims
     r = np.random.default_rng(seed)
     n = sum(int(np.prod(s)) for _, s in fno_ref.layout(C, K, L))
     p = (r.standard_normal(n) * scale / np.sqrt(C)).astype(np.float32)
@@ -87,8 +89,8 @@ def _case(seed=11, scale=0.5):
     return p, now, nxt, norm
 
 
-def _model(p, norm):
-    nx, ny, C, K, L = DIMS
+def _model(p, norm, dims=DIMS):
+    nx, ny, C, K, L = dims
     m = lbm.Surrogate(nx, ny, C, K, L)
     m.set_params(p)
     m.set_norm(*norm)
@@ -99,14 +101,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_advance_against_reference():
-    p, now, _, norm = _case()
-    m = _model(p, norm)
+@pytest.mark.parametrize("dims", [DIMS, TALL])
+def test_advance_against_reference(dims):
+    p, now, _, norm = _case(dims=dims)
+    m = _model(p, norm, dims)
     now_d = torch.from_numpy(now).cuda().contiguous()
     out = torch.empty_like(now_d)
     drift, ok = m.advance(now_d, out, max_drift=1.0)
     got = out.cpu().numpy()
-    ref = fno_ref.advance(p.astype(np.float64), now, DIMS, norm)
+    ref = fno_ref.advance(p.astype(np.float64), now, dims, norm)
     for c in range(6):
         assert _rel(got[c] - now[c], ref[c] - now[c]) < 3e-2, c
     s0, s1 = now[0].sum(), got[0].sum()
@@ -117,15 +120,16 @@ def test_advance_against_reference():
     assert not ok0  # any change of sum(alpha_g) fails a zero tolerance
 
 
-def test_loss_and_gradient_against_reference():
-    p, now, nxt, norm = _case(seed=12)
-    m = _model(p, norm)
+@pytest.mark.parametrize("dims", [DIMS, TALL])
+def test_loss_and_gradient_against_reference(dims):
+    p, now, nxt, norm = _case(seed=12, dims=dims)
+    m = _model(p, norm, dims)
     m.zero_grads()
     loss = m.accumulate(torch.from_numpy(now).cuda().contiguous(), torch.from_numpy(nxt).cuda().contiguous())
     g = m.grads()
-    ref_loss, ref_g = fno_ref.loss_and_grad(p.astype(np.float64), now, nxt, DIMS, norm)
+    ref_loss, ref_g = fno_ref.loss_and_grad(p.astype(np.float64), now, nxt, dims, norm)
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
-    nx, ny, C, K, L = DIMS
+    nx, ny, C, K, L = dims
     at = 0
     for name, shape in fno_ref.layout(C, K, L):
         n = int(np.prod(shape))
