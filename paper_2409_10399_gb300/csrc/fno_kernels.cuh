@@ -22,9 +22,11 @@ typedef __nv_bfloat16 bf16;
 // ksplit > 1 splits K into chunks of kchunk (a multiple of 32) over blocks,
 // each adding alpha times its partial product into a float C with atomics
 // (C += alpha op(A) op(B); beta is not applied).
-// With bias != null (float C only) the epilogue also adds bias[b] (one value
-// per batch entry) to the result, stores it in C and GELU(result) as bf16 at
-// the same index of hout: the last product of a surrogate layer.
+// With bias != null (float C, ksplit 1) the epilogue also adds a bias to the
+// result: bias[b] (one value per batch entry) or, with bias_rows, bias[row].
+// With hout != null it stores act ? GELU(result) : result as bf16 at the same
+// index of hout (the last product of a surrogate layer, the lifting); C may
+// then be null (beta 0), and the float result is not stored.
 struct GemmArgs {
   const bf16 *A, *B;
   void *C;
@@ -34,6 +36,7 @@ struct GemmArgs {
   int ksplit, kchunk;
   const float *bias;
   bf16 *hout;
+  int bias_rows, act;
 };
 
 __device__ __forceinline__ float gelu(float z);
@@ -151,17 +154,18 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     OutT *p = C + (long long)gr * g.ldc + gc;
     if constexpr (std::is_same<OutT, float>::value) {
       if (g.bias) {
-        const float bb = g.bias[b];
+        const float bb = g.bias_rows ? g.bias[gr] : g.bias[b];
+#pragma unroll
+        for (int e = 0; e < 4; e++) o[e] += bb;
+      }
+      if (g.hout) {
         bf16 hv[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-          o[e] += bb;
-          hv[e] = __float2bfloat16(gelu(o[e]));
-        }
+        for (int e = 0; e < 4; e++) hv[e] = __float2bfloat16(g.act ? gelu(o[e]) : o[e]);
         *reinterpret_cast<uint2 *>(g.hout + (long long)b * g.sC + (long long)gr * g.ldc + gc) =
             *reinterpret_cast<const uint2 *>(hv);
       }
-      *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+      if (g.C) *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
       bf16 hv[4] = {__float2bfloat16(o[0]), __float2bfloat16(o[1]), __float2bfloat16(o[2]), __float2bfloat16(o[3])};
       *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(hv);
@@ -181,16 +185,6 @@ __device__ __forceinline__ float gelu_grad(float z) {
   const float u = k * (z + 0.044715f * z * z * z);
   const float t = tanhf(u);
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
-}
-
-// z[c][p] += bias[c]; h = act ? gelu(z) : z, as bf16 (z keeps the biased value)
-__global__ void k_bias_act(float *z, const float *bias, bf16 *h, int C, long long P, int act) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)C * P) return;
-  const int c = (int)(i / P);
-  const float v = z[i] + bias[c];
-  z[i] = v;
-  h[i] = __float2bfloat16(act ? gelu(v) : v);
 }
 
 // dz = act ? dh * gelu'(z) : dh  (float and bf16 copies)
@@ -220,31 +214,29 @@ __global__ void k_bias_grad(const float *dz, float *db, long long P) {
   if (threadIdx.x == 0) atomicAdd(db + c, s[0]);
 }
 
-// squared error of the first `cv` of C channels: d = 2 (y - t) / (cv P)
-// (zero on padding channels), per-block partial sums of (y - t)^2 in part
-__global__ void k_mse(const float *y, const float *t, float *d, bf16 *d16, int cv, long long P, long long n,
+// squared error of the first cv channels: d = scale (y - t) with scale =
+// 2 / (cv P) (the padding channels of d stay zero); grid (blocks over P, cv),
+// one FP64 partial sum of (y - t)^2 per block in part[y * gridDim.x + x]
+__global__ void k_mse(const float *y, const float *t, float *d, bf16 *d16, long long P, float scale,
                       double *part) {
-  __shared__ double s[256];
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double s[8];
+  const long long i = (long long)blockIdx.y * P + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double e2 = 0.0;
-  if (i < n) {
-    const int c = (int)(i / P);
-    float g = 0.0f;
-    if (c < cv) {
-      const float e = y[i] - t[i];
-      e2 = (double)e * e;
-      g = 2.0f * e / (float)((double)cv * P);
-    }
+  if ((long long)blockIdx.x * blockDim.x + threadIdx.x < P) {
+    const float e = y[i] - t[i];
+    e2 = (double)e * e;
+    const float g = scale * e;
     d[i] = g;
     d16[i] = __float2bfloat16(g);
   }
-  s[threadIdx.x] = e2;
+  for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = e2;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += s[w];
+    part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = a;
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
 // Adam (Kingma & Ba) on FP32 master parameters, bias-corrected step size lr_t

@@ -65,8 +65,8 @@ struct lbm_fno {
   long long adam_t = 0;
   bf16 *W_in16 = nullptr, *W_out16 = nullptr, *W16 = nullptr, *Wfx16 = nullptr, *Wfy16 = nullptr;
   bf16 *Bx = nullptr, *Bxi = nullptr, *By = nullptr, *Byi = nullptr;
-  bf16 *x16 = nullptr, *h16 = nullptr, *Hx16 = nullptr, *Hy16 = nullptr, *O16 = nullptr, *y16 = nullptr;
-  float *z = nullptr, *zin = nullptr, *y = nullptr, *tgt = nullptr;
+  bf16 *x16 = nullptr, *h16 = nullptr, *Hx16 = nullptr, *Hy16 = nullptr, *O16 = nullptr;
+  float *z = nullptr, *y = nullptr, *tgt = nullptr;
   float *dy = nullptr, *dh = nullptr, *dz = nullptr, *dWf = nullptr;
   float *coef32 = nullptr;  // FP32 scratch of the split y-axis projections (2K x C x nx)
   bf16 *dy16 = nullptr, *dz16 = nullptr, *dO16 = nullptr, *dH16 = nullptr;
@@ -106,8 +106,9 @@ struct G {
   float alpha = 1.0f, beta = 0.0f;
   bool ta = false, tb = false, out_f32 = true;
   int ksplit = 1;  // > 1: K split over blocks, FP32 atomic accumulation (beta must be 1)
-  const float *bias = nullptr;  // fused epilogue: + bias[batch], GELU into hout
-  bf16 *hout = nullptr;
+  const float *bias = nullptr;  // fused epilogue: + bias[batch] (bias[row] with bias_rows)
+  bf16 *hout = nullptr;         // ... and (act ? GELU : identity) of the result as bf16; C may be null
+  bool bias_rows = false, act = true;
 };
 
 template <bool TA, bool TB, class OutT>
@@ -119,7 +120,8 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
   if (g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1 || g.sA % 8 ||
       g.sB % 8 || g.sC % 8)
     return cudaErrorInvalidValue;
-  if (g.bias && (!g.out_f32 || !g.hout || g.ksplit > 1 || ((uintptr_t)g.hout & 31))) return cudaErrorInvalidValue;
+  if ((g.bias || g.hout) && (!g.out_f32 || g.ksplit > 1 || ((uintptr_t)g.hout & 31))) return cudaErrorInvalidValue;
+  if (!g.C && (!g.hout || g.beta != 0.0f)) return cudaErrorInvalidValue;
   if (((uintptr_t)g.A | (uintptr_t)g.B | (uintptr_t)g.C) & 31) return cudaErrorMisalignedAddress;
   if (g.ksplit > 1 && !g.out_f32) return cudaErrorInvalidValue;
   int ks = g.ksplit < 1 ? 1 : g.ksplit;
@@ -127,7 +129,7 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
   ks = (g.K + kchunk - 1) / kchunk;
   if ((long long)g.batch * ks > 65535) return cudaErrorInvalidValue;
   fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk,
-                  g.bias, g.hout};
+                  g.bias, g.hout, g.bias_rows ? 1 : 0, g.act ? 1 : 0};
   dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
   if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
   else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
@@ -140,32 +142,35 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
 
 // per-channel scales of the state interface
 struct Norm {
-  float mean[6], std_in[6], std_out[6];
+  float mean[6], inv_in[6], std_out[6], inv_out[6];
 };
 
-// x16[c][p] = (state[c][p] - mean[c]) / std_in[c] for c < 6, zero for padding
-__global__ void k_pack_state(const double *state, bf16 *x16, int cin, long long P, Norm nm) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)cin * P) return;
-  const int c = (int)(i / P);
-  float v = 0.0f;
-  if (c < 6) v = (float)((state[i] - (double)nm.mean[c]) / (double)nm.std_in[c]);
-  x16[i] = __float2bfloat16(v);
+// The state kernels run on grids (blocks over P, 6 state channels); the
+// padding channels of x16 and of the target stay zero from creation on.
+
+// x16[c][p] = (state[c][p] - mean[c]) / std_in[c]
+__global__ void k_pack_state(const double *state, bf16 *x16, long long P, Norm nm) {
+  const int c = blockIdx.y;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  x16[c * P + p] = __float2bfloat16((float)(state[c * P + p] - (double)nm.mean[c]) * nm.inv_in[c]);
 }
 
 // target increment in the model's units: t[c][p] = (next - now) / std_out[c]
-__global__ void k_pack_target(const double *now, const double *next, float *t, int cout, long long P, Norm nm) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)cout * P) return;
-  const int c = (int)(i / P);
-  t[i] = c < 6 ? (float)((next[i] - now[i]) / (double)nm.std_out[c]) : 0.0f;
+__global__ void k_pack_target(const double *now, const double *next, float *t, long long P, Norm nm) {
+  const int c = blockIdx.y;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const long long i = c * P + p;
+  t[i] = (float)(next[i] - now[i]) * nm.inv_out[c];
 }
 
 // next = now + std_out * y (FP64 state, FP32 increment)
 __global__ void k_unpack(const double *now, const float *y, double *next, long long P, Norm nm) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 6 * P) return;
-  const int c = (int)(i / P);
+  const int c = blockIdx.y;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const long long i = c * P + p;
   next[i] = now[i] + (double)nm.std_out[c] * (double)y[i];
 }
 
@@ -282,12 +287,11 @@ static int forward(lbm_fno *f) {
   const int C = f->C, L = f->L;
   const long long P = f->P, CP = (long long)C * P;
   const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
-  G a;  // lifting: zin = W_in x
-  a.A = f->W_in16; a.lda = f->cin; a.B = f->x16; a.ldb = (int)P; a.C = f->zin; a.ldc = (int)P;
+  G a;  // lifting: h_0 = W_in x + b_in, stored as bf16 only
+  a.A = f->W_in16; a.lda = f->cin; a.B = f->x16; a.ldb = (int)P; a.C = nullptr; a.ldc = (int)P;
   a.M = C; a.N = (int)P; a.K = f->cin;
+  a.bias = f->p + f->off.b_in; a.bias_rows = true; a.act = false; a.hout = f->h16;
   GTRY(f, a);
-  fno::k_bias_act<<<nblk(CP), 256, 0, f->stream>>>(f->zin, f->p + f->off.b_in, f->h16, C, P, 0);
-  f->launches++;
   for (int l = 0; l < L; l++) {
     const bf16 *h = f->h16 + l * CP;
     float *z = f->z + l * CP;
@@ -300,12 +304,11 @@ static int forward(lbm_fno *f) {
     rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z, f->p + f->off.b[l], f->h16 + (l + 1) * CP);
     if (rc) return rc;
   }
-  G o;  // y = W_out h_L (+ b_out)
+  G o;  // y = W_out h_L + b_out
   o.A = f->W_out16; o.lda = C; o.B = f->h16 + L * CP; o.ldb = (int)P; o.C = f->y; o.ldc = (int)P;
   o.M = f->cout; o.N = (int)P; o.K = C;
+  o.bias = f->p + f->off.b_out; o.bias_rows = true;
   GTRY(f, o);
-  fno::k_bias_act<<<nblk((long long)f->cout * P), 256, 0, f->stream>>>(f->y, f->p + f->off.b_out, f->y16, f->cout, P, 0);
-  f->launches++;
   FTRY(f, cudaGetLastError());
   return LBM_OK;
 }
@@ -382,10 +385,11 @@ static int ksplit_for(long long K) {
 // loss of f->y against f->tgt; gradients accumulated into f->g
 static int backward(lbm_fno *f, double *loss) {
   const int C = f->C, L = f->L;
-  const long long P = f->P, CP = (long long)C * P, nout = (long long)f->cout * P;
+  const long long P = f->P, CP = (long long)C * P;
   const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
-  const unsigned nb = nblk(nout);
-  fno::k_mse<<<nb, 256, 0, f->stream>>>(f->y, f->tgt, f->dy, f->dy16, f->cv, P, nout, f->part);
+  const unsigned nb = nblk(P) * f->cv;
+  fno::k_mse<<<dim3(nblk(P), f->cv), 256, 0, f->stream>>>(f->y, f->tgt, f->dy, f->dy16, P,
+                                                          (float)(2.0 / ((double)f->cv * P)), f->part);
   f->launches++;
   FTRY(f, cudaMemcpyAsync(f->h_part, f->part, nb * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
   G go;  // dW_out += dy h_L^T
@@ -421,7 +425,7 @@ static int backward(lbm_fno *f, double *loss) {
     if (rc) return rc;
   }
   // lifting (no activation)
-  fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, f->zin, f->dz, f->dz16, CP, 0);
+  fno::k_act_back<<<nblk(CP), 256, 0, f->stream>>>(f->dh, nullptr, f->dz, f->dz16, CP, 0);
   fno::k_bias_grad<<<dim3(64, C), 256, 0, f->stream>>>(f->dz, f->g + f->off.b_in, P);
   f->launches += 2;
   G gi;  // dW_in += dz x^T
@@ -476,7 +480,7 @@ int lbm_fno_destroy(lbm_fno *f) {
   if (!f) return LBM_OK;
   cudaStreamSynchronize(f->stream);
   void *bufs[] = {f->p, f->g, f->m, f->v, f->W_in16, f->W_out16, f->W16, f->Wfx16, f->Wfy16, f->Bx, f->Bxi, f->By,
-                  f->Byi, f->x16, f->h16, f->Hx16, f->Hy16, f->O16, f->y16, f->z, f->zin, f->y, f->tgt, f->dy, f->dh,
+                  f->Byi, f->x16, f->h16, f->Hx16, f->Hy16, f->O16, f->z, f->y, f->tgt, f->dy, f->dh,
                   f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red, f->coef32};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -509,8 +513,7 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
       {(void **)&f->Byi, ny * K2 * 2}, {(void **)&f->x16, f->cin * P * 2},
       {(void **)&f->h16, (layers + 1) * CP * 2}, {(void **)&f->Hx16, layers * K2 * C * ny * 2},
       {(void **)&f->Hy16, layers * K2 * C * nx * 2}, {(void **)&f->O16, hmax * 2},
-      {(void **)&f->y16, f->cout * P * 2}, {(void **)&f->z, layers * CP * 4},
-      {(void **)&f->zin, CP * 4}, {(void **)&f->y, f->cout * P * 4},
+      {(void **)&f->z, layers * CP * 4}, {(void **)&f->y, f->cout * P * 4},
       {(void **)&f->tgt, f->cout * P * 4}, {(void **)&f->dy, f->cout * P * 4},
       {(void **)&f->dh, CP * 4}, {(void **)&f->dz, CP * 4}, {(void **)&f->dWf, wf * 4},
       {(void **)&f->dy16, f->cout * P * 2}, {(void **)&f->dz16, CP * 2},
@@ -534,6 +537,11 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
   cudaMemset(f->g, 0, np * 4);
   cudaMemset(f->m, 0, np * 4);
   cudaMemset(f->v, 0, np * 4);
+  // padding channels of the input, target and output gradient stay zero
+  cudaMemset(f->x16, 0, f->cin * P * 2);
+  cudaMemset(f->tgt, 0, f->cout * P * 4);
+  cudaMemset(f->dy, 0, f->cout * P * 4);
+  cudaMemset(f->dy16, 0, f->cout * P * 2);
   std::vector<float> fw, inv;
   basis(nx, modes, fw, inv);
   int rc = upload_bf16(f, fw, f->Bx);
@@ -611,8 +619,9 @@ static Norm norm_of(const lbm_fno *f) {
   Norm nm;
   for (int c = 0; c < 6; c++) {
     nm.mean[c] = f->norm_mean[c];
-    nm.std_in[c] = f->norm_std[c];
+    nm.inv_in[c] = 1.0f / f->norm_std[c];
     nm.std_out[c] = f->out_std[c];
+    nm.inv_out[c] = 1.0f / f->out_std[c];
   }
   return nm;
 }
@@ -621,8 +630,8 @@ int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double
   if (!f || !now || !next) return LBM_EINVAL;
   const long long P = f->P;
   const Norm nm = norm_of(f);
-  k_pack_state<<<nblk((long long)f->cin * P), 256, 0, f->stream>>>(now, f->x16, f->cin, P, nm);
-  k_pack_target<<<nblk((long long)f->cout * P), 256, 0, f->stream>>>(now, next, f->tgt, f->cout, P, nm);
+  k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
+  k_pack_target<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, next, f->tgt, P, nm);
   f->launches += 2;
   int rc = forward(f);
   if (rc) return rc;
@@ -660,11 +669,11 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   if (!f || !now || !next || now == next) return LBM_EINVAL;
   const long long P = f->P;
   const Norm nm = norm_of(f);
-  k_pack_state<<<nblk((long long)f->cin * P), 256, 0, f->stream>>>(now, f->x16, f->cin, P, nm);
+  k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
   f->launches++;
   int rc = forward(f);
   if (rc) return rc;
-  k_unpack<<<nblk(6 * P), 256, 0, f->stream>>>(now, f->y, next, P, nm);
+  k_unpack<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->y, next, P, nm);
   f->launches++;
   FTRY(f, cudaGetLastError());
   // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g
