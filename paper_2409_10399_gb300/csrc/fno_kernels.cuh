@@ -26,7 +26,14 @@ typedef __nv_bfloat16 bf16;
 // result: bias[b] (one value per batch entry) or, with bias_rows, bias[row].
 // With hout != null it stores act ? GELU(result) : result as bf16 at the same
 // index of hout (the last product of a surrogate layer, the lifting); C may
-// then be null (beta 0), and the float result is not stored.
+// then be null (beta 0), and the float result is not stored; store_c = 0
+// keeps C as an input only (beta 1: C is read, the result goes to hout).
+// The SEG2 form (batch 1, ksplit 1) adds a second product to the same tile:
+// C += A2_t B2_t over K2, where for the tile at output columns n0.. (all in
+// one row of seg_nx columns) A2_t = A2 + (n0 / seg_nx) a2_rs is K2 x M
+// (lda2) and B2_t = B2 + (n0 % seg_nx) ldb2 is N x K2 (ldb2), both read
+// transposed: the pointwise product of a layer fused with the reconstruction
+// of its x spectrum, whose coefficients differ from row to row.
 struct GemmArgs {
   const bf16 *A, *B;
   void *C;
@@ -36,14 +43,17 @@ struct GemmArgs {
   int ksplit, kchunk;
   const float *bias;
   bf16 *hout;
-  int bias_rows, act;
+  int bias_rows, act, store_c;
+  const bf16 *A2, *B2;
+  int K2, lda2, ldb2, seg_nx;
+  long long a2_rs;
 };
 
 __device__ __forceinline__ float gelu(float z);
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
 
-template <bool TA, bool TB, class OutT>
+template <bool TA, bool TB, class OutT, bool SEG2 = false>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   using namespace nvcuda;
   // A tile: [GBM][GBK] (TA: [GBK][GBM]); B tile: [GBK][GBN] (TB: [GBN][GBK])
@@ -110,6 +120,47 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     }
     __syncthreads();
   }
+  if constexpr (SEG2) {
+    // second product, both operands transposed: A2_t is [K2][M], B2_t is [N][K2]
+    __shared__ __align__(32) bf16 sA2[GBK][GBM + GPAD];
+    __shared__ __align__(32) bf16 sB2[GBN][GBK + GPAD];
+    typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> FragA2;
+    typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> FragB2;
+    const bf16 *A2 = g.A2 + (long long)(n0 / g.seg_nx) * g.a2_rs;
+    const bf16 *B2 = g.B2 + (long long)(n0 % g.seg_nx) * g.ldb2;
+    for (int k0 = 0; k0 < g.K2; k0 += GBK) {
+#pragma unroll
+      for (int v = tid; v < GBK * GBM / 8; v += 128) {
+        const int r = v / (GBM / 8), c = (v % (GBM / 8)) * 8, ki = k0 + r, mi = m0 + c;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (mi < g.M && ki < g.K2) val = *reinterpret_cast<const uint4 *>(A2 + (long long)ki * g.lda2 + mi);
+        *reinterpret_cast<uint4 *>(&sA2[r][c]) = val;
+      }
+#pragma unroll
+      for (int v = tid; v < GBN * GBK / 8; v += 128) {
+        const int r = v / (GBK / 8), c = (v % (GBK / 8)) * 8, ni = n0 + r, ki = k0 + c;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (ni < g.N && ki < g.K2) val = *reinterpret_cast<const uint4 *>(B2 + (long long)r * g.ldb2 + ki);
+        *reinterpret_cast<uint4 *>(&sB2[r][c]) = val;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; kk += 16) {
+        FragA2 fa[2];
+        FragB2 fb[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+          wmma::load_matrix_sync(fa[i], &sA2[kk][wm + 16 * i], GBM + GPAD);
+          wmma::load_matrix_sync(fb[i], &sB2[wn + 16 * i][kk], GBK + GPAD);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+          for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
 #pragma unroll
   for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -165,7 +216,7 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
         *reinterpret_cast<uint2 *>(g.hout + (long long)b * g.sC + (long long)gr * g.ldc + gc) =
             *reinterpret_cast<const uint2 *>(hv);
       }
-      if (g.C) *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+      if (g.C && g.store_c) *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
       bf16 hv[4] = {__float2bfloat16(o[0]), __float2bfloat16(o[1]), __float2bfloat16(o[2]), __float2bfloat16(o[3])};
       *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(hv);

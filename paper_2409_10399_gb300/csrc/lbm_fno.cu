@@ -108,12 +108,16 @@ struct G {
   int ksplit = 1;  // > 1: K split over blocks, FP32 atomic accumulation (beta must be 1)
   const float *bias = nullptr;  // fused epilogue: + bias[batch] (bias[row] with bias_rows)
   bf16 *hout = nullptr;         // ... and (act ? GELU : identity) of the result as bf16; C may be null
-  bool bias_rows = false, act = true;
+  bool bias_rows = false, act = true, store_c = true;
+  // second product of the same tile (fno::GemmArgs, SEG2): pointwise + x reconstruction
+  const bf16 *A2 = nullptr, *B2 = nullptr;
+  int K2 = 0, lda2 = 0, ldb2 = 0, seg_nx = 0;
+  long long a2_rs = 0;
 };
 
-template <bool TA, bool TB, class OutT>
+template <bool TA, bool TB, class OutT, bool SEG2 = false>
 static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
-  fno::k_gemm<TA, TB, OutT><<<grid, 128, 0, st>>>(a);
+  fno::k_gemm<TA, TB, OutT, SEG2><<<grid, 128, 0, st>>>(a);
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
@@ -122,6 +126,11 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
     return cudaErrorInvalidValue;
   if ((g.bias || g.hout) && (!g.out_f32 || g.ksplit > 1 || ((uintptr_t)g.hout & 31))) return cudaErrorInvalidValue;
   if (!g.C && (!g.hout || g.beta != 0.0f)) return cudaErrorInvalidValue;
+  if (!g.store_c && (!g.hout || !g.C)) return cudaErrorInvalidValue;
+  if (g.A2 && (!g.B2 || g.ta || g.tb || !g.out_f32 || g.batch != 1 || g.ksplit > 1 || g.K2 < 16 || g.K2 % 16 ||
+               g.lda2 % 8 || g.ldb2 % 8 || g.a2_rs % 8 || g.seg_nx < fno::GBN || g.seg_nx % fno::GBN ||
+               g.N % g.seg_nx || g.lda2 < g.M || g.ldb2 < g.K2 || (((uintptr_t)g.A2 | (uintptr_t)g.B2) & 31)))
+    return cudaErrorInvalidValue;
   if (((uintptr_t)g.A | (uintptr_t)g.B | (uintptr_t)g.C) & 31) return cudaErrorMisalignedAddress;
   if (g.ksplit > 1 && !g.out_f32) return cudaErrorInvalidValue;
   int ks = g.ksplit < 1 ? 1 : g.ksplit;
@@ -129,9 +138,11 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
   ks = (g.K + kchunk - 1) / kchunk;
   if ((long long)g.batch * ks > 65535) return cudaErrorInvalidValue;
   fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk,
-                  g.bias, g.hout, g.bias_rows ? 1 : 0, g.act ? 1 : 0};
+                  g.bias, g.hout, g.bias_rows ? 1 : 0, g.act ? 1 : 0, g.store_c ? 1 : 0,
+                  g.A2, g.B2, g.K2, g.lda2, g.ldb2, g.seg_nx, g.a2_rs};
   dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
-  if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
+  if (g.A2) launch_gemm_t<false, false, float, true>(a, grid, st);
+  else if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
   else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
   else if (g.tb) g.out_f32 ? launch_gemm_t<false, true, float>(a, grid, st) : launch_gemm_t<false, true, bf16>(a, grid, st);
   else g.out_f32 ? launch_gemm_t<false, false, float>(a, grid, st) : launch_gemm_t<false, false, bf16>(a, grid, st);
@@ -216,26 +227,42 @@ static int refresh_weights(lbm_fno *f) {
     if (e_ != cudaSuccess) return ferr((f), LBM_ECUDA, "gemm %s (line %d): %s", #gg, __LINE__, cudaGetErrorString(e_)); \
   } while (0)
 
-// z += S^x(h): h is C x (ny x nx) bf16, z is C x (ny x nx) float
-static int spec_x(lbm_fno *f, const bf16 *h, bf16 *Hx, const bf16 *Wf, float *z) {
+// z = W_l h + S^x(h): h is C x (ny x nx) bf16, z is C x (ny x nx) float.
+// The mixed x coefficients are laid out [ny][2K][C], so that for one row y
+// they form the (2K x C) left factor of that row's reconstruction; when nx is
+// a multiple of the 64-column tile the pointwise product and the
+// reconstruction run as one two-segment product and z is written once.
+static int pointwise_and_spec_x(lbm_fno *f, const bf16 *W, const bf16 *h, bf16 *Hx, const bf16 *Wf, float *z) {
   const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
+  const long long P = f->P;
   G a;  // Hx (2K x C ny) = B_x^T h^T
   a.A = f->Bx; a.ta = true; a.lda = K2;
   a.B = h; a.tb = true; a.ldb = nx;
   a.C = Hx; a.out_f32 = false; a.ldc = C * ny;
   a.M = K2; a.N = C * ny; a.K = nx;
   GTRY(f, a);
-  G b;  // per mode: O_k (2C x ny) = Wf_k (2C x 2C) H_k
-  b.A = Wf; b.lda = 2 * C; b.sA = 4LL * C * C;
-  b.B = Hx; b.ldb = ny; b.sB = 2LL * C * ny;
-  b.C = f->O16; b.out_f32 = false; b.ldc = ny; b.sC = 2LL * C * ny;
-  b.M = 2 * C; b.N = ny; b.K = 2 * C; b.batch = f->K;
+  G b;  // per mode k: O[:, k, :] (ny x 2C) = H_k^T Wf_k^T
+  b.A = Hx; b.ta = true; b.lda = ny; b.sA = 2LL * C * ny;
+  b.B = Wf; b.tb = true; b.ldb = 2 * C; b.sB = 4LL * C * C;
+  b.C = f->O16; b.out_f32 = false; b.ldc = K2 * C; b.sC = 2LL * C;
+  b.M = ny; b.N = 2 * C; b.K = 2 * C; b.batch = f->K;
   GTRY(f, b);
-  G c;  // z (C ny x nx) += O^T Bxi^T
-  c.A = f->O16; c.ta = true; c.lda = C * ny;
+  G w;  // z = W h (C x P)
+  w.A = W; w.lda = C; w.B = h; w.ldb = (int)P; w.C = z; w.ldc = (int)P;
+  w.M = C; w.N = (int)P; w.K = C;
+  if (nx % fno::GBN == 0) {
+    // ... + for the tile of row y: O[y]^T (C x 2K) B_xi^T (2K x columns)
+    w.A2 = f->O16; w.lda2 = C; w.a2_rs = (long long)K2 * C;
+    w.B2 = f->Bxi; w.ldb2 = K2; w.K2 = K2; w.seg_nx = nx;
+    GTRY(f, w);
+    return LBM_OK;
+  }
+  GTRY(f, w);
+  G c;  // per row y: z[:, y, :] (C x nx) += O[y]^T B_xi^T
+  c.A = f->O16; c.ta = true; c.lda = C; c.sA = (long long)K2 * C;
   c.B = f->Bxi; c.tb = true; c.ldb = K2;
-  c.C = z; c.ldc = nx; c.beta = 1.0f;
-  c.M = C * ny; c.N = nx; c.K = K2;
+  c.C = z; c.ldc = (int)P; c.sC = nx; c.beta = 1.0f;
+  c.M = C; c.N = nx; c.K = K2; c.batch = ny;
   GTRY(f, c);
   return LBM_OK;
 }
@@ -261,7 +288,8 @@ static int project_y(lbm_fno *f, const bf16 *basis, const bf16 *x, bf16 *out) {
 
 // z += S^y(h); Hy is [2K][C][nx].  The last product of the layer: it also adds
 // the bias and writes GELU(z) into hnext (fused epilogue).
-static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z, const float *bias, bf16 *hnext) {
+static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z, const float *bias, bf16 *hnext,
+                  bool keep_z) {
   const int C = f->C, K2 = 2 * f->K, nx = f->nx, ny = f->ny;
   const long long P = f->P;
   int rc = project_y(f, f->By, h, Hy);  // Hy[:, c, :] (2K x nx) = B_y^T h[c]
@@ -277,13 +305,14 @@ static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z,
   c.B = f->O16; c.ldb = C * nx; c.sB = nx;
   c.C = z; c.ldc = nx; c.sC = P; c.beta = 1.0f;
   c.M = ny; c.N = nx; c.K = K2; c.batch = C;
-  c.bias = bias; c.hout = hnext;
+  c.bias = bias; c.hout = hnext; c.store_c = keep_z;
   GTRY(f, c);
   return LBM_OK;
 }
 
-// forward from f->x16 to f->y (cout x P float); keeps h_l, z_l, Hx_l, Hy_l
-static int forward(lbm_fno *f) {
+// forward from f->x16 to f->y (cout x P float); keeps h_l, Hx_l, Hy_l, and
+// the pre-activations z_l when `train` (the backward pass needs GELU'(z_l))
+static int forward(lbm_fno *f, bool train) {
   const int C = f->C, L = f->L;
   const long long P = f->P, CP = (long long)C * P;
   const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
@@ -295,13 +324,9 @@ static int forward(lbm_fno *f) {
   for (int l = 0; l < L; l++) {
     const bf16 *h = f->h16 + l * CP;
     float *z = f->z + l * CP;
-    G w;  // z = W_l h
-    w.A = f->W16 + (long long)l * C * C; w.lda = C; w.B = h; w.ldb = (int)P; w.C = z; w.ldc = (int)P;
-    w.M = C; w.N = (int)P; w.K = C;
-    GTRY(f, w);
-    int rc = spec_x(f, h, f->Hx16 + l * hx, f->Wfx16 + l * wf, z);
+    int rc = pointwise_and_spec_x(f, f->W16 + (long long)l * C * C, h, f->Hx16 + l * hx, f->Wfx16 + l * wf, z);
     if (rc) return rc;
-    rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z, f->p + f->off.b[l], f->h16 + (l + 1) * CP);
+    rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z, f->p + f->off.b[l], f->h16 + (l + 1) * CP, train);
     if (rc) return rc;
   }
   G o;  // y = W_out h_L + b_out
@@ -633,7 +658,7 @@ int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double
   k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
   k_pack_target<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, next, f->tgt, P, nm);
   f->launches += 2;
-  int rc = forward(f);
+  int rc = forward(f, true);
   if (rc) return rc;
   return backward(f, loss);
 }
@@ -671,7 +696,7 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   const Norm nm = norm_of(f);
   k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
   f->launches++;
-  int rc = forward(f);
+  int rc = forward(f, false);
   if (rc) return rc;
   k_unpack<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->y, next, P, nm);
   f->launches++;

@@ -7,8 +7,10 @@
 - The surrogate step (lbm_fno_advance) against oracle/fno_ref.advance, the
   loss and the parameter gradient (lbm_fno_accumulate) against
   oracle/fno_ref.loss_and_grad (float64, FFT-based, autodiff pinned to finite
-  differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2) and a
-  tall one (32 x 512, L = 1) whose y-axis projections split over blocks.  The
+  differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2: the
+  separate pointwise and x-reconstruction products) and a tall one (64 x 512,
+  L = 1: the two fused into one two-segment product, the y projections split
+  over blocks).  The
   kernels round weights and activations to BF16 (8 significant bits), so the
   bars are relative L2 3e-2 on the state increment and the gradient of every
   parameter block, 2e-2 on the loss.
@@ -26,7 +28,7 @@ from oracle import fno_ref
 pytestmark = pytest.mark.gpu
 
 DIMS = (32, 48, 16, 8, 2)  # nx, ny, C, K, L
-TALL = (32, 512, 16, 8, 1)  # ny >= 512: the y-axis projections split over blocks
+TALL = (64, 512, 16, 8, 1)  # nx % 64 == 0: pointwise + x reconstruction fused; ny >= 512: split y projection
 
 
 def _bf(t):
