@@ -51,17 +51,44 @@ struct GemmArgs {
 
 __device__ __forceinline__ float gelu(float z);
 
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8, GSTAGES = 3;
+
+// 16-byte asynchronous global -> shared copy; with pred false nothing is
+// read (source size 0) and the 16 bytes are zero-filled
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = pred ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <bool TA, bool TB>
+struct GemmSmem {
+  // A tile: [GBM][GBK] (TA: [GBK][GBM]); B tile: [GBK][GBN] (TB: [GBN][GBK])
+  static constexpr int A_ROWS = TA ? GBK : GBM, A_COLS = TA ? GBM : GBK;
+  static constexpr int B_ROWS = TB ? GBN : GBK, B_COLS = TB ? GBK : GBN;
+  static constexpr int A_LD = A_COLS + GPAD, B_LD = B_COLS + GPAD;
+  static constexpr int A_BYTES = A_ROWS * A_LD * 2, B_BYTES = B_ROWS * B_LD * 2;
+  static constexpr int STAGE = (A_BYTES + B_BYTES + 127) / 128 * 128;
+  static constexpr int PIPE = GSTAGES * STAGE;
+  static constexpr int C_BYTES = GBM * (GBN + 4) * 4;
+  static constexpr int SEG2_BYTES = GBK * (GBM + GPAD) * 2 + GBN * (GBK + GPAD) * 2;
+  static constexpr int BYTES = PIPE > C_BYTES ? (PIPE > SEG2_BYTES ? PIPE : SEG2_BYTES)
+                                              : (C_BYTES > SEG2_BYTES ? C_BYTES : SEG2_BYTES);
+};
 
 template <bool TA, bool TB, class OutT, bool SEG2 = false>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   using namespace nvcuda;
-  // A tile: [GBM][GBK] (TA: [GBK][GBM]); B tile: [GBK][GBN] (TB: [GBN][GBK])
-  constexpr int A_ROWS = TA ? GBK : GBM, A_COLS = TA ? GBM : GBK;
-  constexpr int B_ROWS = TB ? GBN : GBK, B_COLS = TB ? GBK : GBN;
-  __shared__ __align__(32) bf16 sA[A_ROWS][A_COLS + GPAD];
-  __shared__ __align__(32) bf16 sB[B_ROWS][B_COLS + GPAD];
-  __shared__ __align__(32) float sC[GBM][GBN + 4];
+  typedef GemmSmem<TA, TB> SM;
+  constexpr int A_ROWS = SM::A_ROWS, A_COLS = SM::A_COLS, B_ROWS = SM::B_ROWS, B_COLS = SM::B_COLS;
+  constexpr int A_LD = SM::A_LD, B_LD = SM::B_LD;
+  // one buffer: a ring of GSTAGES (A, B) tiles for the main product, reused
+  // after it by the second segment's tiles and then by the FP32 output tile
+  __shared__ __align__(128) unsigned char smem[SM::BYTES];
+  float(*sC)[GBN + 4] = reinterpret_cast<float(*)[GBN + 4]>(smem);
 
   const int b = blockIdx.z / g.ksplit, split = blockIdx.z % g.ksplit;
   const int kbeg = split * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
@@ -81,49 +108,64 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 #pragma unroll
     for (int j = 0; j < 2; j++) wmma::fill_fragment(acc[i][j], 0.0f);
 
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    // global -> shared in 16-byte vectors (8 bf16), zero outside the matrix
+  // stage the k-slice starting at k0 into ring slot st, zero outside the matrix
+  auto load_stage = [&](int st, int k0) {
+    bf16 *sA = reinterpret_cast<bf16 *>(smem + st * SM::STAGE);
+    bf16 *sB = reinterpret_cast<bf16 *>(smem + st * SM::STAGE + SM::A_BYTES);
 #pragma unroll
     for (int v = tid; v < A_ROWS * A_COLS / 8; v += 128) {
       const int r = v / (A_COLS / 8), c = (v % (A_COLS / 8)) * 8;
       const int gr = (TA ? k0 : m0) + r, gc = (TA ? m0 : k0) + c;
       const int mi = TA ? gc : gr, ki = TA ? gr : gc;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (mi < g.M && ki < kend) val = *reinterpret_cast<const uint4 *>(A + (long long)gr * g.lda + gc);
-      *reinterpret_cast<uint4 *>(&sA[r][c]) = val;
+      const bool ok = mi < g.M && ki < kend;
+      cp_async16(sA + r * A_LD + c, ok ? A + (long long)gr * g.lda + gc : A, ok);
     }
 #pragma unroll
     for (int v = tid; v < B_ROWS * B_COLS / 8; v += 128) {
       const int r = v / (B_COLS / 8), c = (v % (B_COLS / 8)) * 8;
       const int gr = (TB ? n0 : k0) + r, gc = (TB ? k0 : n0) + c;
       const int ni = TB ? gr : gc, ki = TB ? gc : gr;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (ni < g.N && ki < kend) val = *reinterpret_cast<const uint4 *>(B + (long long)gr * g.ldb + gc);
-      *reinterpret_cast<uint4 *>(&sB[r][c]) = val;
+      const bool ok = ni < g.N && ki < kend;
+      cp_async16(sB + r * B_LD + c, ok ? B + (long long)gr * g.ldb + gc : B, ok);
     }
-    __syncthreads();
+  };
+
+  const int nk = kend > kbeg ? (kend - kbeg + GBK - 1) / GBK : 0;
+#pragma unroll
+  for (int st = 0; st < GSTAGES - 1; st++) {
+    if (st < nk) load_stage(st, kbeg + st * GBK);
+    cp_async_commit();
+  }
+  for (int it = 0; it < nk; it++) {
+    cp_async_wait<GSTAGES - 2>();  // slice `it` has landed (this thread's copies)
+    __syncthreads();               // ... everyone's; and slot (it - 1) % GSTAGES is free
+    if (it + GSTAGES - 1 < nk) load_stage((it + GSTAGES - 1) % GSTAGES, kbeg + (it + GSTAGES - 1) * GBK);
+    cp_async_commit();
+    const bf16 *sA = reinterpret_cast<const bf16 *>(smem + (it % GSTAGES) * SM::STAGE);
+    const bf16 *sB = reinterpret_cast<const bf16 *>(smem + (it % GSTAGES) * SM::STAGE + SM::A_BYTES);
 #pragma unroll
     for (int kk = 0; kk < GBK; kk += 16) {
       FragA fa[2];
       FragB fb[2];
 #pragma unroll
       for (int i = 0; i < 2; i++) {
-        const bf16 *pa = TA ? &sA[kk][wm + 16 * i] : &sA[wm + 16 * i][kk];
-        wmma::load_matrix_sync(fa[i], pa, A_COLS + GPAD);
-        const bf16 *pb = TB ? &sB[wn + 16 * i][kk] : &sB[kk][wn + 16 * i];
-        wmma::load_matrix_sync(fb[i], pb, B_COLS + GPAD);
+        const bf16 *pa = TA ? sA + kk * A_LD + wm + 16 * i : sA + (wm + 16 * i) * A_LD + kk;
+        wmma::load_matrix_sync(fa[i], pa, A_LD);
+        const bf16 *pb = TB ? sB + (wn + 16 * i) * B_LD + kk : sB + kk * B_LD + wn + 16 * i;
+        wmma::load_matrix_sync(fb[i], pb, B_LD);
       }
 #pragma unroll
       for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
+  __syncthreads();  // the ring is free for the second segment and the output tile
   if constexpr (SEG2) {
     // second product, both operands transposed: A2_t is [K2][M], B2_t is [N][K2]
-    __shared__ __align__(32) bf16 sA2[GBK][GBM + GPAD];
-    __shared__ __align__(32) bf16 sB2[GBN][GBK + GPAD];
+    bf16(*sA2)[GBM + GPAD] = reinterpret_cast<bf16(*)[GBM + GPAD]>(smem);
+    bf16(*sB2)[GBK + GPAD] = reinterpret_cast<bf16(*)[GBK + GPAD]>(smem + GBK * (GBM + GPAD) * 2);
     typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> FragA2;
     typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> FragB2;
     const bf16 *A2 = g.A2 + (long long)(n0 / g.seg_nx) * g.a2_rs;
