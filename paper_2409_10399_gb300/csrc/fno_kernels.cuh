@@ -71,15 +71,20 @@ struct GemmSmem {
   static constexpr int B_ROWS = TB ? GBN : GBK, B_COLS = TB ? GBK : GBN;
   static constexpr int A_LD = A_COLS + GPAD, B_LD = B_COLS + GPAD;
   static constexpr int A_BYTES = A_ROWS * A_LD * 2, B_BYTES = B_ROWS * B_LD * 2;
-  static constexpr int STAGE = (A_BYTES + B_BYTES + 127) / 128 * 128;
+  // second segment's tiles (both transposed): [GBK][GBM] and [GBN][GBK]
+  static constexpr int A2_LD = GBM + GPAD, B2_LD = GBK + GPAD, A2_BYTES = GBK * A2_LD * 2;
+  static constexpr int SEG2_BYTES = A2_BYTES + GBN * B2_LD * 2;
+  static constexpr int S1 = A_BYTES + B_BYTES;
+  static constexpr int STAGE = ((S1 > SEG2_BYTES ? S1 : SEG2_BYTES) + 127) / 128 * 128;
   static constexpr int PIPE = GSTAGES * STAGE;
   static constexpr int C_BYTES = GBM * (GBN + 4) * 4;
-  static constexpr int SEG2_BYTES = GBK * (GBM + GPAD) * 2 + GBN * (GBK + GPAD) * 2;
-  static constexpr int BYTES = PIPE > C_BYTES ? (PIPE > SEG2_BYTES ? PIPE : SEG2_BYTES)
-                                              : (C_BYTES > SEG2_BYTES ? C_BYTES : SEG2_BYTES);
+  static constexpr int BYTES = PIPE > C_BYTES ? PIPE : C_BYTES;
 };
 
-template <bool TA, bool TB, class OutT, bool SEG2 = false>
+// PRE (float C, beta != 0, ksplit 1): the old C tile is loaded into
+// registers before the product, so that its read from memory overlaps the
+// operand loads and the tensor-core work instead of following them.
+template <bool TA, bool TB, class OutT, bool SEG2 = false, bool PRE = false>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   using namespace nvcuda;
   typedef GemmSmem<TA, TB> SM;
@@ -97,6 +102,18 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // 2 x 2 warps of 32 x 32
+  // epilogue: groups of 4 columns (N and ldc are multiples of 8), PER per thread
+  constexpr int PER = GBM * GBN / 4 / 128;
+  float4 pre[PRE ? PER : 1];
+  if constexpr (PRE) {
+    const float *Cb = reinterpret_cast<const float *>(g.C) + (long long)b * g.sC;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
+      pre[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < g.M && gc < g.N) pre[j] = *reinterpret_cast<const float4 *>(Cb + (long long)gr * g.ldc + gc);
+    }
+  }
 
   typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16,
                          typename std::conditional<TA, wmma::col_major, wmma::row_major>::type> FragA;
@@ -130,79 +147,87 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     }
   };
 
-  const int nk = kend > kbeg ? (kend - kbeg + GBK - 1) / GBK : 0;
+  // the second segment's k-slices follow the first's through the same ring
+  const bf16 *A2 = nullptr, *B2 = nullptr;
+  if constexpr (SEG2) {
+    A2 = g.A2 + (long long)(n0 / g.seg_nx) * g.a2_rs;
+    B2 = g.B2 + (long long)(n0 % g.seg_nx) * g.ldb2;
+  }
+  auto load_stage2 = [&](int st, int k0) {
+    bf16 *sA2 = reinterpret_cast<bf16 *>(smem + st * SM::STAGE);
+    bf16 *sB2 = reinterpret_cast<bf16 *>(smem + st * SM::STAGE + SM::A2_BYTES);
+#pragma unroll
+    for (int v = tid; v < GBK * GBM / 8; v += 128) {
+      const int r = v / (GBM / 8), c = (v % (GBM / 8)) * 8, ki = k0 + r, mi = m0 + c;
+      const bool ok = mi < g.M && ki < g.K2;
+      cp_async16(sA2 + r * SM::A2_LD + c, ok ? A2 + (long long)ki * g.lda2 + mi : A2, ok);
+    }
+#pragma unroll
+    for (int v = tid; v < GBN * GBK / 8; v += 128) {
+      const int r = v / (GBK / 8), c = (v % (GBK / 8)) * 8, ni = n0 + r, ki = k0 + c;
+      const bool ok = ni < g.N && ki < g.K2;
+      cp_async16(sB2 + r * SM::B2_LD + c, ok ? B2 + (long long)r * g.ldb2 + ki : B2, ok);
+    }
+  };
+  const int nk1 = kend > kbeg ? (kend - kbeg + GBK - 1) / GBK : 0;
+  const int nk = nk1 + (SEG2 ? (g.K2 + GBK - 1) / GBK : 0);
+  auto load_slice = [&](int st, int it) {
+    if (!SEG2 || it < nk1) load_stage(st, kbeg + it * GBK);
+    else load_stage2(st, (it - nk1) * GBK);
+  };
 #pragma unroll
   for (int st = 0; st < GSTAGES - 1; st++) {
-    if (st < nk) load_stage(st, kbeg + st * GBK);
+    if (st < nk) load_slice(st, st);
     cp_async_commit();
   }
   for (int it = 0; it < nk; it++) {
     cp_async_wait<GSTAGES - 2>();  // slice `it` has landed (this thread's copies)
     __syncthreads();               // ... everyone's; and slot (it - 1) % GSTAGES is free
-    if (it + GSTAGES - 1 < nk) load_stage((it + GSTAGES - 1) % GSTAGES, kbeg + (it + GSTAGES - 1) * GBK);
+    if (it + GSTAGES - 1 < nk) load_slice((it + GSTAGES - 1) % GSTAGES, it + GSTAGES - 1);
     cp_async_commit();
-    const bf16 *sA = reinterpret_cast<const bf16 *>(smem + (it % GSTAGES) * SM::STAGE);
-    const bf16 *sB = reinterpret_cast<const bf16 *>(smem + (it % GSTAGES) * SM::STAGE + SM::A_BYTES);
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      FragA fa[2];
-      FragB fb[2];
-#pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const bf16 *pa = TA ? sA + kk * A_LD + wm + 16 * i : sA + (wm + 16 * i) * A_LD + kk;
-        wmma::load_matrix_sync(fa[i], pa, A_LD);
-        const bf16 *pb = TB ? sB + (wn + 16 * i) * B_LD + kk : sB + kk * B_LD + wn + 16 * i;
-        wmma::load_matrix_sync(fb[i], pb, B_LD);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-    }
-  }
-  cp_async_wait<0>();
-  __syncthreads();  // the ring is free for the second segment and the output tile
-  if constexpr (SEG2) {
-    // second product, both operands transposed: A2_t is [K2][M], B2_t is [N][K2]
-    bf16(*sA2)[GBM + GPAD] = reinterpret_cast<bf16(*)[GBM + GPAD]>(smem);
-    bf16(*sB2)[GBK + GPAD] = reinterpret_cast<bf16(*)[GBK + GPAD]>(smem + GBK * (GBM + GPAD) * 2);
-    typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> FragA2;
-    typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> FragB2;
-    const bf16 *A2 = g.A2 + (long long)(n0 / g.seg_nx) * g.a2_rs;
-    const bf16 *B2 = g.B2 + (long long)(n0 % g.seg_nx) * g.ldb2;
-    for (int k0 = 0; k0 < g.K2; k0 += GBK) {
-#pragma unroll
-      for (int v = tid; v < GBK * GBM / 8; v += 128) {
-        const int r = v / (GBM / 8), c = (v % (GBM / 8)) * 8, ki = k0 + r, mi = m0 + c;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (mi < g.M && ki < g.K2) val = *reinterpret_cast<const uint4 *>(A2 + (long long)ki * g.lda2 + mi);
-        *reinterpret_cast<uint4 *>(&sA2[r][c]) = val;
-      }
-#pragma unroll
-      for (int v = tid; v < GBN * GBK / 8; v += 128) {
-        const int r = v / (GBK / 8), c = (v % (GBK / 8)) * 8, ni = n0 + r, ki = k0 + c;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (ni < g.N && ki < g.K2) val = *reinterpret_cast<const uint4 *>(B2 + (long long)r * g.ldb2 + ki);
-        *reinterpret_cast<uint4 *>(&sB2[r][c]) = val;
-      }
-      __syncthreads();
+    const unsigned char *slot = smem + (it % GSTAGES) * SM::STAGE;
+    if (!SEG2 || it < nk1) {
+      const bf16 *sA = reinterpret_cast<const bf16 *>(slot);
+      const bf16 *sB = reinterpret_cast<const bf16 *>(slot + SM::A_BYTES);
 #pragma unroll
       for (int kk = 0; kk < GBK; kk += 16) {
-        FragA2 fa[2];
-        FragB2 fb[2];
+        FragA fa[2];
+        FragB fb[2];
 #pragma unroll
         for (int i = 0; i < 2; i++) {
-          wmma::load_matrix_sync(fa[i], &sA2[kk][wm + 16 * i], GBM + GPAD);
-          wmma::load_matrix_sync(fb[i], &sB2[wn + 16 * i][kk], GBK + GPAD);
+          const bf16 *pa = TA ? sA + kk * A_LD + wm + 16 * i : sA + (wm + 16 * i) * A_LD + kk;
+          wmma::load_matrix_sync(fa[i], pa, A_LD);
+          const bf16 *pb = TB ? sB + (wn + 16 * i) * B_LD + kk : sB + kk * B_LD + wn + 16 * i;
+          wmma::load_matrix_sync(fb[i], pb, B_LD);
         }
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
           for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
       }
-      __syncthreads();
+    } else if constexpr (SEG2) {
+      typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> FragA2;
+      typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> FragB2;
+      const bf16 *sA2 = reinterpret_cast<const bf16 *>(slot);
+      const bf16 *sB2 = reinterpret_cast<const bf16 *>(slot + SM::A2_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < GBK; kk += 16) {
+        FragA2 fa[2];
+        FragB2 fb[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+          wmma::load_matrix_sync(fa[i], sA2 + kk * SM::A2_LD + wm + 16 * i, SM::A2_LD);
+          wmma::load_matrix_sync(fb[i], sB2 + (wn + 16 * i) * SM::B2_LD + kk, SM::B2_LD);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+          for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+      }
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();  // the ring is free for the output tile
 #pragma unroll
   for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -212,7 +237,6 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   OutT *C = reinterpret_cast<OutT *>(g.C) + (long long)b * g.sC;
   // epilogue in groups of 4 columns (N and ldc are multiples of 8): every read
   // of the old C is issued before any write, so the reads overlap
-  constexpr int PER = GBM * GBN / 4 / 128;
   if constexpr (std::is_same<OutT, float>::value) {
     if (g.ksplit > 1) {
       for (int v = tid; v < GBM * GBN; v += 128) {
@@ -227,7 +251,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   for (int j = 0; j < PER; j++) {
     const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
     old[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g.beta != 0.0f && gr < g.M && gc < g.N) {
+    if constexpr (PRE) {
+      old[j] = pre[j];
+    } else if (g.beta != 0.0f && gr < g.M && gc < g.N) {
       const OutT *p = C + (long long)gr * g.ldc + gc;
       if constexpr (std::is_same<OutT, float>::value) {
         old[j] = *reinterpret_cast<const float4 *>(p);
@@ -268,15 +294,22 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 
 // ---------------------------------------------------------------- elementwise
 
+// hardware tanh (PTX tanh.approx.f32, relative error ~2^-11): below the
+// 2^-9 of the BF16 activations it feeds
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float gelu(float z) {
   // tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
   const float k = 0.7978845608028654f;
-  return 0.5f * z * (1.0f + tanhf(k * (z + 0.044715f * z * z * z)));
+  return 0.5f * z * (1.0f + tanh_fast(k * (z + 0.044715f * z * z * z)));
 }
 __device__ __forceinline__ float gelu_grad(float z) {
   const float k = 0.7978845608028654f;
   const float u = k * (z + 0.044715f * z * z * z);
-  const float t = tanhf(u);
+  const float t = tanh_fast(u);
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
 }
 

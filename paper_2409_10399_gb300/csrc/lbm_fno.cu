@@ -115,9 +115,9 @@ struct G {
   long long a2_rs = 0;
 };
 
-template <bool TA, bool TB, class OutT, bool SEG2 = false>
+template <bool TA, bool TB, class OutT, bool SEG2 = false, bool PRE = false>
 static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
-  fno::k_gemm<TA, TB, OutT, SEG2><<<grid, 128, 0, st>>>(a);
+  fno::k_gemm<TA, TB, OutT, SEG2, PRE><<<grid, 128, 0, st>>>(a);
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
@@ -141,7 +141,12 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
                   g.bias, g.hout, g.bias_rows ? 1 : 0, g.act ? 1 : 0, g.store_c ? 1 : 0,
                   g.A2, g.B2, g.K2, g.lda2, g.ldb2, g.seg_nx, g.a2_rs};
   dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
+  const bool pre = g.out_f32 && g.beta != 0.0f && ks == 1;  // accumulate into C: prefetch the old tile
   if (g.A2) launch_gemm_t<false, false, float, true>(a, grid, st);
+  else if (pre && g.ta && g.tb) launch_gemm_t<true, true, float, false, true>(a, grid, st);
+  else if (pre && g.ta) launch_gemm_t<true, false, float, false, true>(a, grid, st);
+  else if (pre && g.tb) launch_gemm_t<false, true, float, false, true>(a, grid, st);
+  else if (pre) launch_gemm_t<false, false, float, false, true>(a, grid, st);
   else if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
   else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
   else if (g.tb) g.out_f32 ? launch_gemm_t<false, true, float>(a, grid, st) : launch_gemm_t<false, true, bf16>(a, grid, st);
