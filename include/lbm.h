@@ -316,8 +316,9 @@ int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double
 int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, float grad_scale);
 /* Surrogate step: next = now + std_out * model(now) (device states, distinct
  * buffers).  *drift = relative change of the per-phase volumes sum(alpha_g)
- * and sum(1 - alpha_g) (the larger; infinite if non-finite); *ok = drift <=
- * max_drift.  A caller that gets ok = 0 advances the state with the LBM
+ * and sum(1 - alpha_g) (the larger; infinite if any value of the new state
+ * is not finite); *ok = drift <= max_drift.  Synchronises the stream (the
+ * host reads the FP64 sums).  A caller that gets ok = 0 advances the state with the LBM
  * instead (the surrogate's fallback). */
 int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok);
 int lbm_fno_launch_count(const lbm_fno *f, long long *n);

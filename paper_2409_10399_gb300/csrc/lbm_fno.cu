@@ -190,19 +190,24 @@ __global__ void k_unpack(const double *now, const float *y, double *next, long l
   next[i] = now[i] + (double)nm.std_out[c] * (double)y[i];
 }
 
-// FP64 sums of alpha_g over the field (block partials), for the mass check
-__global__ void k_sum(const double *a, long long n, double *part) {
-  __shared__ double s[256];
+// FP64 sums for the checks of a call, block partials in
+// part[y * gridDim.x + x]: alpha_g before (blockIdx.y = 0) and after (1) the
+// call, and all six channels after it (2; finite only if every value is)
+__global__ void k_sum3(const double *a0, const double *a1, long long n, double *part) {
+  __shared__ double s[8];
+  const double *a = blockIdx.y == 0 ? a0 : a1;
+  const long long m = blockIdx.y == 2 ? 6 * n : n;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
     acc += a[i];
-  s[threadIdx.x] = acc;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s[w];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
 // ------------------------------------------------------------------ model pieces
@@ -548,7 +553,7 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
       {(void **)&f->dh, CP * 4}, {(void **)&f->dz, CP * 4}, {(void **)&f->dWf, wf * 4},
       {(void **)&f->dy16, f->cout * P * 2}, {(void **)&f->dz16, CP * 2},
       {(void **)&f->dO16, hmax * 2}, {(void **)&f->dH16, hmax * 2},
-      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 2048 * 8},
+      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 3 * 640 * 8},
       {(void **)&f->coef32, K2 * C * nx * 4}};
   for (auto &a : al) {
     if (cudaMalloc(a.p, (size_t)a.bytes) != cudaSuccess) {
@@ -558,7 +563,7 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
     }
   }
   if (cudaMallocHost((void **)&f->h_part, (size_t)nblk((long long)f->cout * P) * 8) != cudaSuccess ||
-      cudaMallocHost((void **)&f->h_red, 2048 * 8) != cudaSuccess) {
+      cudaMallocHost((void **)&f->h_red, 3 * 640 * 8) != cudaSuccess) {
     cudaGetLastError();
     lbm_fno_destroy(f);
     return LBM_ENOMEM;
@@ -682,16 +687,20 @@ int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, floa
   return refresh_weights(f);
 }
 
-// FP64 sum of n values (fixed-order two-level reduction), synchronises
-static int dsum(lbm_fno *f, const double *a, long long n, double *out) {
-  const int blocks = 1024;
-  k_sum<<<blocks, 256, 0, f->stream>>>(a, n, f->red);
+// The three sums of k_sum3 (fixed-order reductions) with one
+// synchronisation: s[0] = sum alpha_g of now, s[1] of next, s[2] = sum of
+// every value of next
+static int check_sums(lbm_fno *f, const double *now, const double *next, double s[3]) {
+  const int blocks = 640;
+  k_sum3<<<dim3(blocks, 3), 256, 0, f->stream>>>(now, next, f->P, f->red);
   f->launches++;
-  FTRY(f, cudaMemcpyAsync(f->h_red, f->red, blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  FTRY(f, cudaMemcpyAsync(f->h_red, f->red, 3 * blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
   FTRY(f, cudaStreamSynchronize(f->stream));
-  double s = 0.0;
-  for (int i = 0; i < blocks; i++) s += f->h_red[i];
-  *out = s;
+  for (int k = 0; k < 3; k++) {
+    double t = 0.0;
+    for (int i = 0; i < blocks; i++) t += f->h_red[k * blocks + i];
+    s[k] = t;
+  }
   return LBM_OK;
 }
 
@@ -706,13 +715,14 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   k_unpack<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->y, next, P, nm);
   f->launches++;
   FTRY(f, cudaGetLastError());
-  // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g
-  double g0 = 0, g1 = 0;
-  rc = dsum(f, now, P, &g0);
-  if (!rc) rc = dsum(f, next, P, &g1);
+  // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g;
+  // a non-finite value anywhere in the new state fails the check too
+  double sm[3];
+  rc = check_sums(f, now, next, sm);
   if (rc) return rc;
+  const double g0 = sm[0], g1 = sm[1];
   const double dg = fabs(g1 - g0) / fmax(g0, 1e-300), dl = fabs(g1 - g0) / fmax((double)P - g0, 1e-300);
-  const double d = isfinite(g1) ? fmax(dg, dl) : INFINITY;
+  const double d = isfinite(sm[2]) ? fmax(dg, dl) : INFINITY;
   if (drift) *drift = d;
   if (ok) *ok = d <= max_drift;
   return LBM_OK;

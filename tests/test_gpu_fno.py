@@ -120,6 +120,10 @@ def test_advance_against_reference(dims):
     assert ok == (expect <= 1.0)
     _, ok0 = m.advance(now_d, out, max_drift=0.0)
     assert not ok0  # any change of sum(alpha_g) fails a zero tolerance
+    bad = now_d.clone()
+    bad[3, 5] = float("nan")  # a liquid velocity, not alpha_g
+    d_bad, ok_bad = m.advance(bad, out, max_drift=1e30)
+    assert not ok_bad and d_bad == float("inf")
 
 
 @pytest.mark.parametrize("dims", [DIMS, TALL])
