@@ -317,10 +317,25 @@ int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, floa
 /* Surrogate step: next = now + std_out * model(now) (device states, distinct
  * buffers).  *drift = relative change of the per-phase volumes sum(alpha_g)
  * and sum(1 - alpha_g) (the larger; infinite if any value of the new state
- * is not finite); *ok = drift <= max_drift.  Synchronises the stream (the
+ * is not finite); *ok = drift <= max_drift and every new alpha_g in [0, 1].  Synchronises the stream (the
  * host reads the FP64 sums).  A caller that gets ok = 0 advances the state with the LBM
  * instead (the surrogate's fallback). */
 int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok);
+/* One surrogate window on a live lattice: the surrogate's use with the LBM as
+ * its fallback.  `ctx` must be a D2Q9 lattice of the model's nx x ny,
+ * initialised, at an even time t (populations in their natural slots);
+ * `window` (even) is the number of LBM steps one model call stands for (64
+ * for the trained workload model).  The lattice's moments go through
+ * lbm_fno_advance; when its check passes (*used = 1) the lattice is
+ * re-initialised from the predicted fields exactly as lbm_init does
+ * (equilibrium populations, held sources re-latched) and its clock set to
+ * t + window; otherwise (*used = 0) the lattice advances `window` LBM steps
+ * from its own populations (lbm_step).  *drift as for lbm_fno_advance.
+ * LBM_EINVAL for a lattice of another type or size or an odd window,
+ * LBM_ESTATE for an odd time or a lattice in error.  Uses the model's stream
+ * for the model and the lattice's stream for the lattice; synchronises both.
+ * Not in the paper. */
+int lbm_surrogate_advance(lbm_ctx *ctx, lbm_fno *model, int window, double max_drift, double *drift, int *used);
 int lbm_fno_launch_count(const lbm_fno *f, long long *n);
 const char *lbm_fno_last_error(const lbm_fno *f);
 int lbm_fno_destroy(lbm_fno *f);

@@ -94,6 +94,7 @@ def load_library(build_if_missing=True):
             "lbm_fno_accumulate": (I, [P, dp, dp, ctypes.POINTER(D)]),
             "lbm_fno_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
             "lbm_fno_advance": (I, [P, dp, dp, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
+            "lbm_surrogate_advance": (I, [P, P, I, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "lbm_fno_launch_count": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_fno_last_error": (ctypes.c_char_p, [P]),
             "lbm_fno_destroy": (I, [P]),
@@ -495,6 +496,19 @@ class Surrogate:
         self._check(self._lib.lbm_fno_advance(self._h, self._state(now), self._state(out), float(max_drift),
                                               ctypes.byref(d), ctypes.byref(ok)), "lbm_fno_advance")
         return d.value, bool(ok.value)
+
+    def advance_lattice(self, sim, window=64, max_drift=1e-4):
+        """One window on a live Simulation (lbm_surrogate_advance): the
+        surrogate's state when its check passes, else `window` LBM steps;
+        returns (drift, used)."""
+        d = ctypes.c_double()
+        used = ctypes.c_int()
+        rc = self._lib.lbm_surrogate_advance(sim._h, self._h, int(window), float(max_drift), ctypes.byref(d),
+                                             ctypes.byref(used))
+        if rc != 0:
+            msgs = [self._lib.lbm_last_error(sim._h), self._lib.lbm_fno_last_error(self._h)]
+            raise LBMError(rc, "lbm_surrogate_advance: " + "; ".join(m.decode() for m in msgs if m))
+        return d.value, bool(used.value)
 
     @property
     def launches(self):

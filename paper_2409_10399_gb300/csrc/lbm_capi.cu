@@ -70,6 +70,7 @@ __global__ void k_diag_final(const double *partials, int nblocks, double *out) {
 
 using namespace lbm;
 
+#include "lbm_ctx_access.h"
 #include "lbm_internal.h"
 
 static int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
@@ -328,6 +329,17 @@ cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const
   if (lattice == 2) return launch_batch_step_2(prec, args, work, nwork, block, parity, latch, off32, st);
   return launch_batch_step_3(prec, args, work, nwork, block, parity, latch, off32, st);
 }
+}  // namespace lbm
+
+namespace lbm {
+void ctx_window_info(const lbm_ctx *c, int *lattice, int n[3], long long *t, int *ready) {
+  *lattice = c->lattice;
+  for (int d = 0; d < 3; d++) n[d] = c->n[d];
+  *t = c->t;
+  *ready = c->initialised && !c->sticky;
+}
+void ctx_set_time(lbm_ctx *c, long long t) { c->t = t; }
+int ctx_error(lbm_ctx *c, int code, const char *msg) { return set_err(c, code, "%s", msg); }
 }  // namespace lbm
 
 extern "C" {

@@ -25,6 +25,7 @@
 
 #include "../../include/lbm.h"
 #include "fno_kernels.cuh"
+#include "lbm_ctx_access.h"
 
 using fno::bf16;
 
@@ -71,6 +72,7 @@ struct lbm_fno {
   float *coef32 = nullptr;  // FP32 scratch of the split y-axis projections (2K x C x nx)
   bf16 *dy16 = nullptr, *dz16 = nullptr, *dO16 = nullptr, *dH16 = nullptr;
   double *part = nullptr, *h_part = nullptr, *red = nullptr, *h_red = nullptr;
+  double *st = nullptr;  // FP64 states of lbm_surrogate_advance (now, next), allocated on first use
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t stream = 0;
   long long launches = 0;
@@ -192,14 +194,17 @@ __global__ void k_unpack(const double *now, const float *y, double *next, long l
 
 // FP64 sums for the checks of a call, block partials in
 // part[y * gridDim.x + x]: alpha_g before (blockIdx.y = 0) and after (1) the
-// call, and all six channels after it (2; finite only if every value is)
-__global__ void k_sum3(const double *a0, const double *a1, long long n, double *part) {
+// call, all six channels after it (2; finite only if every value is), and
+// the number of new alpha_g values outside [0, 1] (3)
+__global__ void k_checks(const double *a0, const double *a1, long long n, double *part) {
   __shared__ double s[8];
   const double *a = blockIdx.y == 0 ? a0 : a1;
   const long long m = blockIdx.y == 2 ? 6 * n : n;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
-    acc += a[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    acc += blockIdx.y == 3 ? (v >= 0.0 && v <= 1.0 ? 0.0 : 1.0) : v;
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -516,7 +521,7 @@ int lbm_fno_destroy(lbm_fno *f) {
   cudaStreamSynchronize(f->stream);
   void *bufs[] = {f->p, f->g, f->m, f->v, f->W_in16, f->W_out16, f->W16, f->Wfx16, f->Wfy16, f->Bx, f->Bxi, f->By,
                   f->Byi, f->x16, f->h16, f->Hx16, f->Hy16, f->O16, f->z, f->y, f->tgt, f->dy, f->dh,
-                  f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red, f->coef32};
+                  f->dz, f->dWf, f->dy16, f->dz16, f->dO16, f->dH16, f->part, f->red, f->coef32, f->st};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (f->h_part) cudaFreeHost(f->h_part);
@@ -553,7 +558,7 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
       {(void **)&f->dh, CP * 4}, {(void **)&f->dz, CP * 4}, {(void **)&f->dWf, wf * 4},
       {(void **)&f->dy16, f->cout * P * 2}, {(void **)&f->dz16, CP * 2},
       {(void **)&f->dO16, hmax * 2}, {(void **)&f->dH16, hmax * 2},
-      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 3 * 640 * 8},
+      {(void **)&f->part, (long long)nblk((long long)f->cout * P) * 8}, {(void **)&f->red, 4 * 640 * 8},
       {(void **)&f->coef32, K2 * C * nx * 4}};
   for (auto &a : al) {
     if (cudaMalloc(a.p, (size_t)a.bytes) != cudaSuccess) {
@@ -563,7 +568,7 @@ int lbm_fno_create(int nx, int ny, int channels, int modes, int layers, lbm_fno 
     }
   }
   if (cudaMallocHost((void **)&f->h_part, (size_t)nblk((long long)f->cout * P) * 8) != cudaSuccess ||
-      cudaMallocHost((void **)&f->h_red, 3 * 640 * 8) != cudaSuccess) {
+      cudaMallocHost((void **)&f->h_red, 4 * 640 * 8) != cudaSuccess) {
     cudaGetLastError();
     lbm_fno_destroy(f);
     return LBM_ENOMEM;
@@ -687,16 +692,16 @@ int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, floa
   return refresh_weights(f);
 }
 
-// The three sums of k_sum3 (fixed-order reductions) with one
+// The four sums of k_checks (fixed-order reductions) with one
 // synchronisation: s[0] = sum alpha_g of now, s[1] of next, s[2] = sum of
-// every value of next
-static int check_sums(lbm_fno *f, const double *now, const double *next, double s[3]) {
+// every value of next, s[3] = number of new alpha_g outside [0, 1]
+static int check_sums(lbm_fno *f, const double *now, const double *next, double s[4]) {
   const int blocks = 640;
-  k_sum3<<<dim3(blocks, 3), 256, 0, f->stream>>>(now, next, f->P, f->red);
+  k_checks<<<dim3(blocks, 4), 256, 0, f->stream>>>(now, next, f->P, f->red);
   f->launches++;
-  FTRY(f, cudaMemcpyAsync(f->h_red, f->red, 3 * blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  FTRY(f, cudaMemcpyAsync(f->h_red, f->red, 4 * blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
   FTRY(f, cudaStreamSynchronize(f->stream));
-  for (int k = 0; k < 3; k++) {
+  for (int k = 0; k < 4; k++) {
     double t = 0.0;
     for (int i = 0; i < blocks; i++) t += f->h_red[k * blocks + i];
     s[k] = t;
@@ -716,16 +721,48 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   f->launches++;
   FTRY(f, cudaGetLastError());
   // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g;
-  // a non-finite value anywhere in the new state fails the check too
-  double sm[3];
+  // a non-finite value anywhere in the new state, or a volume fraction
+  // outside [0, 1], fails the check too
+  double sm[4];
   rc = check_sums(f, now, next, sm);
   if (rc) return rc;
   const double g0 = sm[0], g1 = sm[1];
   const double dg = fabs(g1 - g0) / fmax(g0, 1e-300), dl = fabs(g1 - g0) / fmax((double)P - g0, 1e-300);
   const double d = isfinite(sm[2]) ? fmax(dg, dl) : INFINITY;
   if (drift) *drift = d;
-  if (ok) *ok = d <= max_drift;
+  if (ok) *ok = d <= max_drift && sm[3] == 0.0;
   return LBM_OK;
+}
+
+int lbm_surrogate_advance(lbm_ctx *ctx, lbm_fno *f, int window, double max_drift, double *drift, int *used) {
+  if (!ctx || !f) return LBM_EINVAL;
+  if (used) *used = 0;
+  int lattice, n[3], ready;
+  long long t0;
+  lbm::ctx_window_info(ctx, &lattice, n, &t0, &ready);
+  if (lattice != LBM_D2Q9 || n[0] != f->nx || n[1] != f->ny || n[2] != 1)
+    return lbm::ctx_error(ctx, LBM_EINVAL, "lbm_surrogate_advance: the lattice is not a D2Q9 grid of the model's size");
+  if (window < 2 || window % 2) return lbm::ctx_error(ctx, LBM_EINVAL, "lbm_surrogate_advance: window must be even");
+  if (!ready) return lbm::ctx_error(ctx, LBM_ESTATE, "lbm_surrogate_advance: lattice not initialised or in error");
+  if (t0 % 2) return lbm::ctx_error(ctx, LBM_ESTATE, "lbm_surrogate_advance: odd time (populations mid-swap)");
+  const long long P = f->P;
+  if (!f->st) FTRY(f, cudaMalloc((void **)&f->st, 12 * P * sizeof(double)));
+  double *now = f->st, *next = f->st + 6 * P;
+  int rc = lbm_get_moments(ctx, now, now + P, now + 3 * P, now + 5 * P, nullptr, nullptr, 1);
+  if (rc) return rc;
+  double d = 0.0;
+  int ok = 0;
+  rc = lbm_fno_advance(f, now, next, max_drift, &d, &ok);
+  if (rc) return rc;
+  if (drift) *drift = d;
+  if (ok) {
+    rc = lbm_init(ctx, next, next + P, next + 3 * P, next + 5 * P, 1);
+    if (rc) return rc;
+    lbm::ctx_set_time(ctx, t0 + window);
+    if (used) *used = 1;
+    return LBM_OK;
+  }
+  return lbm_step(ctx, window);  // the fallback: the lattice's own populations
 }
 
 int lbm_fno_launch_count(const lbm_fno *f, long long *n) {

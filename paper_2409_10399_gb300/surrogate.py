@@ -186,14 +186,12 @@ def evaluate(model, data, max_drift=1e-4, rollout=8):
                 fallback_rate=fallbacks / max(1, len(drifts)), rollout_alpha_rel_l2=roll)
 
 
-def advance_with_fallback(model, sim, now, out, max_drift=1e-4):
-    """One 64-step window: the surrogate, or the LBM when the volume check fails."""
-    d, ok = model.advance(now, out, max_drift=max_drift)
-    if not ok:
-        sim.init(**_views(now))
-        sim.step(WINDOW)
-        sim.moments(out=_views(out))
-    return ok, d
+def advance_with_fallback(model, sim, max_drift=1e-4):
+    """One 64-step window of a live Simulation: the surrogate, or the LBM from
+    the lattice's own populations when the check fails
+    (lbm_surrogate_advance).  Returns (used, drift)."""
+    d, used = model.advance_lattice(sim, WINDOW, max_drift)
+    return used, d
 
 
 def speed(model, state, nx, ny, reps=20):

@@ -163,3 +163,60 @@ def test_adam_step_is_the_textbook_update():
     got = m.params()
     assert np.allclose(got, ref, rtol=1e-5, atol=1e-7)
     assert np.abs(m.grads()).max() == 0.0  # zeroed after the step
+
+
+def _lattice(dims=DIMS, seed=5):
+    import lbm_inputs
+    from paper_2409_10399_gb300 import surrogate as S
+    nx, ny = dims[0], dims[1]
+    sim = lbm.Simulation("D2Q9", (nx, ny), S._lbm_params("fp64"))
+    sim.init(**lbm_inputs.fields_plumes(nx, ny, seed))
+    return sim
+
+
+def _state_of(sim):
+    m = sim.moments()
+    return np.concatenate([m["alpha_g"][None], m["u_g"], m["u_l"], m["p_k"][None]])
+
+
+def test_surrogate_window_on_a_lattice_takes_the_model_state():
+    p, _, _, norm = _case(seed=14)
+    m = _model(p, norm)
+    sim = _lattice()
+    now = _state_of(sim)
+    drift, used = m.advance_lattice(sim, 64, max_drift=1e30)
+    assert used and sim.t == 64
+    # the same fields through lbm_init on a twin lattice: identical moments
+    pred = torch.empty((6, now.shape[1]), dtype=torch.float64, device="cuda")
+    d2, _ = m.advance(torch.from_numpy(now).cuda().contiguous(), pred, max_drift=1e30)
+    assert d2 == drift
+    pred = pred.cpu().numpy()
+    twin = _lattice()
+    twin.init(alpha_g=pred[0], u_g=pred[1:3], u_l=pred[3:5], p_k=pred[5])
+    assert np.array_equal(_state_of(sim), _state_of(twin))
+
+
+def test_surrogate_window_falls_back_to_the_lattice_steps():
+    p, _, _, norm = _case(seed=15)
+    m = _model(p, norm)
+    sim, twin = _lattice(), _lattice()
+    drift, used = m.advance_lattice(sim, 64, max_drift=0.0)  # any volume change fails
+    assert not used and drift > 0.0 and sim.t == 64
+    twin.step(64)
+    assert np.array_equal(_state_of(sim), _state_of(twin))  # the LBM from its own populations
+
+
+def test_surrogate_window_rejects_other_lattices_and_odd_times():
+    p, _, _, norm = _case(seed=16)
+    m = _model(p, norm)
+    sim = _lattice()
+    sim.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        m.advance_lattice(sim, 64)
+    assert e.value.code == -7  # LBM_ESTATE: populations mid-swap at odd t
+    with pytest.raises(lbm.LBMError) as e:
+        m.advance_lattice(_lattice((48, 32)), 64)
+    assert e.value.code == -1  # LBM_EINVAL: not the model's grid
+    with pytest.raises(lbm.LBMError) as e:
+        m.advance_lattice(_lattice(), 63)
+    assert e.value.code == -1
