@@ -2,7 +2,7 @@
 operator (lbm_fno_*) trained on trajectories of the library's own 2D LBM, that
 advances the state by 64 LBM steps per call, with the LBM as fallback.
 
-    python -m paper_2409_10399_gb300.surrogate [--train 32] [--test 4] [--epochs 12]
+    python -m paper_2409_10399_gb300.surrogate [--train 96] [--test 8] [--epochs 16]
 
 Workload (lbm_inputs "surrogate2d"): D2Q9 256 x 1024, FP32, R = 1000, the
 box2d physics in a closed box (periodic x, walls y), so that the per-phase
@@ -17,8 +17,11 @@ Evaluation on held-out trajectories, per 64-step window and over rollouts of
 chained surrogate calls: relative L2 error of the predicted increment against
 the LBM's increment for each channel, of the state, the persistence baseline
 (next = now) for context, and the fallback rate (per-phase volume drift above
-1e-4 -> the window is advanced with the LBM instead).  Speed: device time of
-one surrogate call against 64 LBM steps (FP32) of the same state.
+1e-4 -> the window is advanced with the LBM instead).  Hybrid runs: live
+lattices advanced window by window through lbm_surrogate_advance (surrogate,
+or the LBM from the lattice's own populations when the check fails), judged
+against the plain LBM's snapshots.  Speed: device time of one surrogate call
+against 64 LBM steps (FP32) of the same state.
 One JSON line per result.
 """
 import argparse
@@ -194,6 +197,41 @@ def advance_with_fallback(model, sim, max_drift=1e-4):
     return used, d
 
 
+def hybrid(model, data, windows=8, max_drift=1e-4):
+    """Live lattices advanced window by window through lbm_surrogate_advance
+    (the surrogate, or 64 LBM steps when its check fails), judged against the
+    plain LBM's snapshots of the same trajectories: alpha_g and state errors
+    after each window, the share of windows the surrogate served, and the
+    device time per window (host synchronisations included)."""
+    import torch
+    n, nsnap, P = data.shape[0], data.shape[1], data.shape[3]
+    nx, ny = model.nx, model.ny
+    windows = min(windows, nsnap - 1)
+    err_a = np.zeros(windows)
+    err_s = np.zeros(windows)
+    used_n, t_ms = 0, 0.0
+    cur = torch.empty((6, P), dtype=torch.float64, device="cuda")
+    for i in range(n):
+        sim = Simulation("D2Q9", (nx, ny, 1), _lbm_params())
+        sim.set_stream(torch.cuda.current_stream())
+        sim.init(**_views(data[i, 0]))
+        for k in range(windows):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            used, _ = advance_with_fallback(model, sim, max_drift)
+            e1.record()
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            used_n += int(used)
+            sim.moments(out=_views(cur))
+            ref = data[i, k + 1]
+            err_a[k] += _rel(cur[0], ref[0]) / n
+            err_s[k] += _rel(cur[:5], ref[:5]) / n
+        sim.close()
+    return dict(windows=n * windows, surrogate_share=used_n / (n * windows), ms_per_window=t_ms / (n * windows),
+                alpha_rel_l2=err_a.tolist(), state_rel_l2=err_s.tolist())
+
+
 def speed(model, state, nx, ny, reps=20):
     """Device time of a surrogate call and of 64 LBM steps on the same state."""
     import torch
@@ -240,16 +278,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--ny", type=int, default=1024)
-    ap.add_argument("--train", type=int, default=32)
-    ap.add_argument("--test", type=int, default=4)
+    ap.add_argument("--train", type=int, default=96)
+    ap.add_argument("--test", type=int, default=8)
     ap.add_argument("--steps", type=int, default=4096)
-    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--speed-only", action="store_true", help="time one surrogate call and 64 LBM steps, no training")
+    ap.add_argument("--save", help="write the trained parameters and normalisation to this .npz")
+    ap.add_argument("--load", help="skip training: parameters and normalisation from this .npz (from --save)")
     args = ap.parse_args()
     emit = lambda d: print(json.dumps(d), flush=True)
     if args.speed_only:
@@ -266,16 +306,25 @@ def main():
               pairs=args.train * (train_data.shape[1] - 1), wall_s=time.time() - t0))
     m = Surrogate(args.nx, args.ny, args.channels, args.modes, args.layers)
     m.set_stream(torch.cuda.current_stream())
-    m.set_params(init_params(args.channels, args.modes, args.layers))
-    mean, std, dstd = fit_norm(train_data)
+    if args.load:
+        z = np.load(args.load)
+        params, (mean, std, dstd) = z["params"], (z["mean"], z["std"], z["dstd"])
+    else:
+        params = init_params(args.channels, args.modes, args.layers)
+        mean, std, dstd = fit_norm(train_data)
+    m.set_params(params)
     m.set_norm(mean, std, dstd)
     emit(dict(stage="model", params=m.num_params, norm_mean=mean.tolist(), norm_std=std.tolist(),
-              increment_std=dstd.tolist()))
-    t1 = time.time()
-    hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))
-    emit(dict(stage="trained", epochs=args.epochs, final_loss=hist[-1], wall_s=time.time() - t1))
+              increment_std=dstd.tolist(), loaded=bool(args.load)))
+    if not args.load:
+        t1 = time.time()
+        hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))
+        emit(dict(stage="trained", epochs=args.epochs, final_loss=hist[-1], wall_s=time.time() - t1))
+    if args.save:
+        np.savez(args.save, params=m.params(), mean=mean, std=std, dstd=dstd)
     ev = evaluate(m, test_data)
     emit(dict(stage="test", **ev))
+    emit(dict(stage="hybrid", **hybrid(m, test_data)))
     sp = speed(m, test_data[0, 0].contiguous(), args.nx, args.ny)
     # every failed check costs the surrogate call and then the 64 LBM steps
     t_eff = sp["surrogate_ms"] + ev["fallback_rate"] * sp["lbm_64_steps_ms"]
