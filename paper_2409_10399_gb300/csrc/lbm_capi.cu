@@ -331,6 +331,23 @@ cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const
 }
 }  // namespace lbm
 
+// Equilibrium populations from device fields whose alpha_g (all in [0, 1])
+// sums to alpha_sum: the deviation reference is its mean; clock at 0.
+static int init_fields(lbm_ctx *c, const double *da, const double *dug, const double *dul, const double *dpk,
+                       double alpha_sum) {
+  c->r_ag = alpha_sum / (double)c->N;
+  c->r_al = 1.0 - c->r_ag;
+  c->t = 0;
+  MomArgs ma = make_mom(c, nullptr);
+  CUDA_TRY(c, dispatch_init(c, ma, da, dug, dul, dpk));
+  c->mass0 = alpha_sum;
+  c->initialised = 1;
+  c->sticky = 0;
+  c->diag_pending = 0;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
 namespace lbm {
 void ctx_window_info(const lbm_ctx *c, int *lattice, int n[3], long long *t, int *ready) {
   *lattice = c->lattice;
@@ -339,6 +356,10 @@ void ctx_window_info(const lbm_ctx *c, int *lattice, int n[3], long long *t, int
   *ready = c->initialised && !c->sticky;
 }
 void ctx_set_time(lbm_ctx *c, long long t) { c->t = t; }
+int ctx_init_device(lbm_ctx *c, const double *alpha_g, const double *u_g, const double *u_l, const double *p_k,
+                    double alpha_sum) {
+  return init_fields(c, alpha_g, u_g, u_l, p_k, alpha_sum);
+}
 int ctx_error(lbm_ctx *c, int code, const char *msg) { return set_err(c, code, "%s", msg); }
 }  // namespace lbm
 
@@ -456,8 +477,6 @@ int lbm_init(lbm_ctx *c, const double *alpha_g, const double *u_g, const double 
     if (!(ah[i] >= 0.0 && ah[i] <= 1.0)) return set_err(c, LBM_EINVAL, "lbm_init: alpha_g[%lld] outside [0,1]", i);
     sum += ah[i];
   }
-  c->r_ag = sum / (double)N;
-  c->r_al = 1.0 - c->r_ag;
   const double *da = alpha_g, *dug = u_g, *dul = u_l, *dpk = p_k;
   if (!on_device) {
     int rc = ensure_stage(c, (size_t)(2 + 2 * D) * N * sizeof(double));
@@ -472,15 +491,7 @@ int lbm_init(lbm_ctx *c, const double *alpha_g, const double *u_g, const double 
     dul = s + (1 + D) * N;
     dpk = s + (1 + 2 * D) * N;
   }
-  c->t = 0;
-  MomArgs ma = make_mom(c, nullptr);
-  CUDA_TRY(c, dispatch_init(c, ma, da, dug, dul, dpk));
-  c->mass0 = sum;
-  c->initialised = 1;
-  c->sticky = 0;
-  c->diag_pending = 0;
-  c->err[0] = 0;
-  return LBM_OK;
+  return init_fields(c, da, dug, dul, dpk, sum);
 }
 
 // Check the diagnostics a previous lbm_step enqueued, if they have arrived.

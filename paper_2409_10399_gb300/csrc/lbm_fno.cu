@@ -73,6 +73,7 @@ struct lbm_fno {
   bf16 *dy16 = nullptr, *dz16 = nullptr, *dO16 = nullptr, *dH16 = nullptr;
   double *part = nullptr, *h_part = nullptr, *red = nullptr, *h_red = nullptr;
   double *st = nullptr;  // FP64 states of lbm_surrogate_advance (now, next), allocated on first use
+  double last_sums[4] = {0, 0, 0, 0};  // the check sums of the last lbm_fno_advance
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t stream = 0;
   long long launches = 0;
@@ -726,6 +727,7 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   double sm[4];
   rc = check_sums(f, now, next, sm);
   if (rc) return rc;
+  for (int k = 0; k < 4; k++) f->last_sums[k] = sm[k];
   const double g0 = sm[0], g1 = sm[1];
   const double dg = fabs(g1 - g0) / fmax(g0, 1e-300), dl = fabs(g1 - g0) / fmax((double)P - g0, 1e-300);
   const double d = isfinite(sm[2]) ? fmax(dg, dl) : INFINITY;
@@ -756,7 +758,8 @@ int lbm_surrogate_advance(lbm_ctx *ctx, lbm_fno *f, int window, double max_drift
   if (rc) return rc;
   if (drift) *drift = d;
   if (ok) {
-    rc = lbm_init(ctx, next, next + P, next + 3 * P, next + 5 * P, 1);
+    // the check verified every new alpha_g in [0, 1] and summed them on the device
+    rc = lbm::ctx_init_device(ctx, next, next + P, next + 3 * P, next + 5 * P, f->last_sums[1]);
     if (rc) return rc;
     lbm::ctx_set_time(ctx, t0 + window);
     if (used) *used = 1;
