@@ -209,6 +209,8 @@ def hybrid(model, data, windows=8, max_drift=1e-4):
     windows = min(windows, nsnap - 1)
     err_a = np.zeros(windows)
     err_s = np.zeros(windows)
+    used_k = np.zeros(windows, dtype=int)
+    drifts = []
     used_n, t_ms = 0, 0.0
     cur = torch.empty((6, P), dtype=torch.float64, device="cuda")
     for i in range(n):
@@ -218,18 +220,21 @@ def hybrid(model, data, windows=8, max_drift=1e-4):
         for k in range(windows):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            used, _ = advance_with_fallback(model, sim, max_drift)
+            used, d = advance_with_fallback(model, sim, max_drift)
             e1.record()
             torch.cuda.synchronize()
             t_ms += e0.elapsed_time(e1)
             used_n += int(used)
+            used_k[k] += int(used)
+            drifts.append(d)
             sim.moments(out=_views(cur))
             ref = data[i, k + 1]
             err_a[k] += _rel(cur[0], ref[0]) / n
             err_s[k] += _rel(cur[:5], ref[:5]) / n
         sim.close()
     return dict(windows=n * windows, surrogate_share=used_n / (n * windows), ms_per_window=t_ms / (n * windows),
-                alpha_rel_l2=err_a.tolist(), state_rel_l2=err_s.tolist())
+                served_per_window=used_k.tolist(), drift_median=float(np.median(drifts)),
+                drift_max=float(np.max(drifts)), alpha_rel_l2=err_a.tolist(), state_rel_l2=err_s.tolist())
 
 
 def speed(model, state, nx, ny, reps=20):
