@@ -311,6 +311,13 @@ int lbm_fno_set_stream(lbm_fno *f, void *cuda_stream);
  * and its gradient added to the accumulated gradients.  `now`, `next`: FP64
  * device states. */
 int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double *loss);
+/* Weight lambda >= 0 of the loss's conservation term (default 0): the loss
+ * of lbm_fno_accumulate becomes the mean squared error plus
+ * lambda * (mean over the nodes of y_0 - t_0)^2, channel 0 being alpha_g in
+ * the model's units; it penalises the error of the window's change of
+ * sum(alpha_g), the quantity the volume check of lbm_fno_advance tests.
+ * LBM_EINVAL for a negative or non-finite weight. */
+int lbm_fno_set_loss(lbm_fno *f, double cons_weight);
 /* Adam step (Kingma & Ba, bias-corrected) with the accumulated gradients
  * times grad_scale, then gradients zeroed and the BF16 weights refreshed. */
 int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, float grad_scale);

@@ -18,7 +18,8 @@ W_k = A_k + i B_k the layer returns irfft of G_k = conj(W_k) F_k (zero above
 K).  In real terms this is the coefficient pair (c_k, s_k) = (Re F_k, -Im F_k)
 mixed by [[A, -B], [B, A]] and summed back as (1/n)(c_0) + (2/n) sum_k
 (c_k cos + s_k sin), the library's form.  GELU is the tanh approximation.
-Loss: mean over the 6 state channels and all nodes of (y - t)^2.
+Loss: mean over the 6 state channels and all nodes of (y - t)^2, plus
+cons * (mean over the nodes of y_0 - t_0)^2 (channel 0 is alpha_g).
 Parity unpinned beyond the finite-difference and identity pins listed in the
 test file (the surrogate is not the paper's method).
 """
@@ -95,13 +96,13 @@ def pack(now, nxt, nx, ny, mean, std_in, std_out):
     return torch.from_numpy(x), torch.from_numpy(t)
 
 
-def loss_and_grad(params, now, nxt, dims, norm):
+def loss_and_grad(params, now, nxt, dims, norm, cons=0.0):
     """FP64 loss and gradient (numpy, the library's parameter order)."""
     nx, ny, C, K, L = dims
     x, t = pack(now, nxt, nx, ny, *norm)
     p = torch.tensor(np.asarray(params, np.float64), requires_grad=True)
     y = forward(p, x, C, K, L)
-    loss = ((y[:CV] - t[:CV]) ** 2).mean()
+    loss = ((y[:CV] - t[:CV]) ** 2).mean() + cons * (y[0] - t[0]).mean() ** 2
     loss.backward()
     return float(loss.detach()), p.grad.numpy().copy()
 

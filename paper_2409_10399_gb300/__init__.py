@@ -92,6 +92,7 @@ def load_library(build_if_missing=True):
                                      ctypes.POINTER(ctypes.c_float)]),
             "lbm_fno_set_stream": (I, [P, P]),
             "lbm_fno_accumulate": (I, [P, dp, dp, ctypes.POINTER(D)]),
+            "lbm_fno_set_loss": (I, [P, D]),
             "lbm_fno_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
             "lbm_fno_advance": (I, [P, dp, dp, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "lbm_surrogate_advance": (I, [P, P, I, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
@@ -478,6 +479,10 @@ class Surrogate:
         if not (_is_torch(t) and t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
             raise ValueError("states are contiguous float64 CUDA tensors of shape (6, nx*ny)")
         return ctypes.c_void_p(t.data_ptr())
+
+    def set_loss(self, cons_weight):
+        """Weight of the conservation term of the loss (lbm_fno_set_loss)."""
+        self._check(self._lib.lbm_fno_set_loss(self._h, float(cons_weight)), "lbm_fno_set_loss")
 
     def accumulate(self, now, nxt):
         loss = ctypes.c_double()

@@ -340,29 +340,61 @@ __global__ void k_bias_grad(const float *dz, float *db, long long P) {
   if (threadIdx.x == 0) atomicAdd(db + c, s[0]);
 }
 
+// sum over a block of 256 threads (8 warps), result in thread 0
+__device__ __forceinline__ double block_sum(double v, double *s8) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double a = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += s8[w];
+  return a;
+}
+
 // squared error of the first cv channels: d = scale (y - t) with scale =
 // 2 / (cv P) (the padding channels of d stay zero); grid (blocks over P, cv),
-// one FP64 partial sum of (y - t)^2 per block in part[y * gridDim.x + x]
+// one FP64 partial sum of (y - t)^2 per block in part[y * gridDim.x + x], and
+// for channel 0 (alpha_g) the partial sums of (y - t) in
+// part[cv * gridDim.x + x]
 __global__ void k_mse(const float *y, const float *t, float *d, bf16 *d16, long long P, float scale,
                       double *part) {
   __shared__ double s[8];
   const long long i = (long long)blockIdx.y * P + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double e2 = 0.0;
+  double e1 = 0.0, e2 = 0.0;
   if ((long long)blockIdx.x * blockDim.x + threadIdx.x < P) {
     const float e = y[i] - t[i];
+    e1 = e;
     e2 = (double)e * e;
     const float g = scale * e;
     d[i] = g;
     d16[i] = __float2bfloat16(g);
   }
-  for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = e2;
-  __syncthreads();
+  const double a2 = block_sum(e2, s);
+  if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = a2;
+  if (blockIdx.y == 0) {
+    __syncthreads();
+    const double a1 = block_sum(e1, s);
+    if (threadIdx.x == 0) part[(long long)gridDim.y * gridDim.x + blockIdx.x] = a1;
+  }
+}
+
+// conservation term of the loss, lambda (mean_p e_0)^2 with e_0 = y_0 - t_0
+// (the alpha_g channel): its gradient 2 lambda mean(e_0) / P is added to
+// every node of channel 0 of d (and d16).  esum: the nb partial sums of e_0
+// from k_mse, reduced in the same order by every block.
+__global__ void k_cons_grad(const double *esum, int nb, float *d, bf16 *d16, long long P, double lambda) {
+  __shared__ double tot;
   if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) a += s[w];
-    part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = a;
+    for (int i = 0; i < nb; i++) a += esum[i];
+    tot = a;
   }
+  __syncthreads();
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float g = d[p] + (float)(2.0 * lambda * (tot / (double)P) / (double)P);
+  d[p] = g;
+  d16[p] = __float2bfloat16(g);
 }
 
 // Adam (Kingma & Ba) on FP32 master parameters, bias-corrected step size lr_t

@@ -74,6 +74,7 @@ struct lbm_fno {
   double *part = nullptr, *h_part = nullptr, *red = nullptr, *h_red = nullptr;
   double *st = nullptr;  // FP64 states of lbm_surrogate_advance (now, next), allocated on first use
   double last_sums[4] = {0, 0, 0, 0};  // the check sums of the last lbm_fno_advance
+  double cons = 0.0;                   // weight of the loss's conservation term
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t stream = 0;
   long long launches = 0;
@@ -428,11 +429,15 @@ static int backward(lbm_fno *f, double *loss) {
   const int C = f->C, L = f->L;
   const long long P = f->P, CP = (long long)C * P;
   const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
-  const unsigned nb = nblk(P) * f->cv;
-  fno::k_mse<<<dim3(nblk(P), f->cv), 256, 0, f->stream>>>(f->y, f->tgt, f->dy, f->dy16, P,
-                                                          (float)(2.0 / ((double)f->cv * P)), f->part);
+  const unsigned nb = nblk(P) * f->cv, nb0 = nblk(P);
+  fno::k_mse<<<dim3(nb0, f->cv), 256, 0, f->stream>>>(f->y, f->tgt, f->dy, f->dy16, P,
+                                                      (float)(2.0 / ((double)f->cv * P)), f->part);
   f->launches++;
-  FTRY(f, cudaMemcpyAsync(f->h_part, f->part, nb * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  if (f->cons > 0.0) {
+    fno::k_cons_grad<<<nb0, 256, 0, f->stream>>>(f->part + nb, (int)nb0, f->dy, f->dy16, P, f->cons);
+    f->launches++;
+  }
+  FTRY(f, cudaMemcpyAsync(f->h_part, f->part, (nb + nb0) * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
   G go;  // dW_out += dy h_L^T
   go.A = f->dy16; go.lda = (int)P; go.B = f->h16 + L * CP; go.tb = true; go.ldb = (int)P;
   go.C = f->g + f->off.W_out; go.ldc = C; go.beta = 1.0f; go.ksplit = ksplit_for(P);
@@ -477,7 +482,10 @@ static int backward(lbm_fno *f, double *loss) {
   FTRY(f, cudaStreamSynchronize(f->stream));
   double s = 0.0;
   for (unsigned i = 0; i < nb; i++) s += f->h_part[i];
-  if (loss) *loss = s / ((double)f->cv * P);
+  double e0 = 0.0;
+  for (unsigned i = 0; i < nb0; i++) e0 += f->h_part[nb + i];
+  const double mean_e0 = e0 / (double)P;
+  if (loss) *loss = s / ((double)f->cv * P) + f->cons * mean_e0 * mean_e0;
   FTRY(f, cudaGetLastError());
   return LBM_OK;
 }
@@ -665,6 +673,12 @@ static Norm norm_of(const lbm_fno *f) {
     nm.inv_out[c] = 1.0f / f->out_std[c];
   }
   return nm;
+}
+
+int lbm_fno_set_loss(lbm_fno *f, double cons_weight) {
+  if (!f || !(cons_weight >= 0.0) || !isfinite(cons_weight)) return LBM_EINVAL;
+  f->cons = cons_weight;
+  return LBM_OK;
 }
 
 int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double *loss) {

@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--cons", type=float, default=0.0,
+                    help="weight of the loss's conservation term (lbm_fno_set_loss)")
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--layers", type=int, default=4)
@@ -319,8 +321,9 @@ def main():
         mean, std, dstd = fit_norm(train_data)
     m.set_params(params)
     m.set_norm(mean, std, dstd)
+    m.set_loss(args.cons)
     emit(dict(stage="model", params=m.num_params, norm_mean=mean.tolist(), norm_std=std.tolist(),
-              increment_std=dstd.tolist(), loaded=bool(args.load)))
+              increment_std=dstd.tolist(), loaded=bool(args.load), cons=args.cons))
     if not args.load:
         t1 = time.time()
         hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))

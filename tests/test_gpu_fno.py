@@ -126,14 +126,15 @@ def test_advance_against_reference(dims):
     assert not ok_bad and d_bad == float("inf")
 
 
-@pytest.mark.parametrize("dims", [DIMS, TALL])
-def test_loss_and_gradient_against_reference(dims):
+@pytest.mark.parametrize("dims,cons", [(DIMS, 0.0), (TALL, 0.0), (DIMS, 50.0)])
+def test_loss_and_gradient_against_reference(dims, cons):
     p, now, nxt, norm = _case(seed=12, dims=dims)
     m = _model(p, norm, dims)
+    m.set_loss(cons)
     m.zero_grads()
     loss = m.accumulate(torch.from_numpy(now).cuda().contiguous(), torch.from_numpy(nxt).cuda().contiguous())
     g = m.grads()
-    ref_loss, ref_g = fno_ref.loss_and_grad(p.astype(np.float64), now, nxt, dims, norm)
+    ref_loss, ref_g = fno_ref.loss_and_grad(p.astype(np.float64), now, nxt, dims, norm, cons)
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss, (loss, ref_loss)
     nx, ny, C, K, L = dims
     at = 0

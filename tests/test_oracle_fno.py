@@ -30,16 +30,17 @@ def _rand(dims, seed, scale=0.3):
     return p, now, nxt, norm
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("cons", [0.0, 30.0])
+def test_gradient_matches_finite_differences(cons):
     dims = (16, 12, 4, 3, 2)
     p, now, nxt, norm = _rand(dims, 1)
-    loss, g = fno_ref.loss_and_grad(p, now, nxt, dims, norm)
+    loss, g = fno_ref.loss_and_grad(p, now, nxt, dims, norm, cons)
     r = np.random.default_rng(2)
     for _ in range(4):
         d = r.standard_normal(p.size)
         eps = 1e-6
-        lp, _ = fno_ref.loss_and_grad(p + eps * d, now, nxt, dims, norm)
-        lm, _ = fno_ref.loss_and_grad(p - eps * d, now, nxt, dims, norm)
+        lp, _ = fno_ref.loss_and_grad(p + eps * d, now, nxt, dims, norm, cons)
+        lm, _ = fno_ref.loss_and_grad(p - eps * d, now, nxt, dims, norm, cons)
         fd = (lp - lm) / (2 * eps)
         assert abs(fd - g @ d) <= 1e-6 * max(1.0, abs(fd)), (fd, g @ d)
 
@@ -78,6 +79,25 @@ def test_imaginary_unit_weight_turns_cosine_into_sine():
     B = torch.eye(C, dtype=torch.float64).repeat(K, 1, 1)
     out = fno_ref.spectral(torch.from_numpy(h), A, B, -1, K).numpy()
     assert np.allclose(out, np.sin(2 * np.pi * k * x / nx)[None, None, :].repeat(ny, 1).repeat(C, 0), atol=1e-12)
+
+
+def test_zero_model_loss_is_the_target_moments():
+    # all parameters zero: y = 0, so the loss is mean(t^2) over the six state
+    # channels plus cons * mean(t_0)^2, and the gradient of the output bias
+    # b_out[c] is -2 mean(t_c) / 6 (+ the conservation term's -2 cons mean(t_0) on c = 0)
+    dims = (8, 8, 4, 2, 1)
+    _, now, nxt, norm = _rand(dims, 4)
+    n = sum(int(np.prod(s)) for _, s in fno_ref.layout(4, 2, 1))
+    _, t = fno_ref.pack(now, nxt, 8, 8, *norm)
+    t = t.numpy()
+    cons = 7.0
+    loss, g = fno_ref.loss_and_grad(np.zeros(n), now, nxt, dims, norm, cons)
+    assert np.isclose(loss, (t[:6] ** 2).mean() + cons * t[0].mean() ** 2, rtol=1e-12)
+    gb = g[-16:]
+    expect = -2.0 * t[:6].mean(axis=(1, 2)) / 6.0
+    expect[0] -= 2.0 * cons * t[0].mean()
+    assert np.allclose(gb[:6], expect, rtol=1e-10, atol=1e-14)
+    assert np.all(gb[6:] == 0.0)
 
 
 def test_parameter_count_of_the_workload_model():
