@@ -126,7 +126,12 @@ def test_advance_against_reference(dims):
     assert not ok_bad and d_bad == float("inf")
 
 
-@pytest.mark.parametrize("dims,cons", [(DIMS, 0.0), (TALL, 0.0), (DIMS, 50.0)])
+# cons = 5: the conservation term's gradient (a uniform 2 cons mean(e_0) / P on
+# the alpha_g channel) then outweighs the squared error's on that channel,
+# while the input blocks whose BF16-rounded inputs sum to nearly zero over the
+# nodes (W_in's p_k column) stay inside the bar; at cons = 50 that column's
+# cancellation against BF16 rounding reached 3.6 %.
+@pytest.mark.parametrize("dims,cons", [(DIMS, 0.0), (TALL, 0.0), (DIMS, 5.0)])
 def test_loss_and_gradient_against_reference(dims, cons):
     p, now, nxt, norm = _case(seed=12, dims=dims)
     m = _model(p, norm, dims)
