@@ -12,7 +12,9 @@ check means something; initial states are gas plumes at random places
 steps with a snapshot every 64: 64 (state, state 64 steps later) pairs.
 
 Training: one sample per forward/backward (lbm_fno_accumulate), gradients
-averaged over a batch of samples, Adam with a cosine-decayed learning rate.
+averaged over a batch of samples, Adam with a cosine-decayed learning rate;
+the loss carries a conservation term of weight --cons (lbm_fno_set_loss) on
+the error of the window's change of sum(alpha_g).
 Evaluation on held-out trajectories, per 64-step window and over rollouts of
 chained surrogate calls: relative L2 error of the predicted increment against
 the LBM's increment for each channel, of the state, the persistence baseline
@@ -289,7 +291,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=16)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--cons", type=float, default=0.0,
+    ap.add_argument("--cons", type=float, default=100.0,
                     help="weight of the loss's conservation term (lbm_fno_set_loss)")
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--modes", type=int, default=32)
