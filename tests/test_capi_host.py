@@ -90,3 +90,21 @@ def test_tile_limit_matches_launch_bounds():
         lbm.tile_limit(4, "fp32")
     with pytest.raises(lbm.LBMError):
         lbm.tile_limit("D2Q9", 7)
+
+
+def test_surrogate_create_rejects_invalid_shapes_without_gpu():
+    """lbm_fno_create validates its shape before touching the device: sizes
+    not multiples of 16, channels not multiples of 16, modes not multiples of
+    8 or above n / 2, and layer counts outside 1..16 give LBM_EINVAL; NULL
+    handles are rejected by every surrogate entry point."""
+    lib = lbm.load_library()
+    h = ctypes.c_void_p()
+    for args in [(24, 32, 16, 8, 1), (32, 40, 16, 8, 1), (32, 32, 24, 8, 1), (32, 32, 16, 12, 1),
+                 (32, 32, 16, 24, 1), (32, 32, 16, 8, 0), (32, 32, 16, 8, 17), (8, 32, 16, 8, 1)]:
+        assert lib.lbm_fno_create(*args, ctypes.byref(h)) == -1, args
+        assert not h.value
+    assert lib.lbm_fno_create(32, 32, 16, 8, 1, None) == -1
+    assert lib.lbm_fno_set_loss(None, ctypes.c_double(1.0)) == -1
+    assert lib.lbm_fno_advance(None, None, None, ctypes.c_double(1e-4), None, None) == -1
+    assert lib.lbm_surrogate_advance(None, None, 64, ctypes.c_double(1e-4), None, None) == -1
+    assert lib.lbm_fno_destroy(None) == 0
