@@ -189,14 +189,15 @@ __device__ __forceinline__ int face_rule(const StepArgs &a, const Geo &g, int q)
   return rule;
 }
 
-// Slot of the read of direction q (AA rule, see the file comment).
-template <class L>
+// Slot of the read of direction q (AA rule, see the file comment).  INT:
+// the node is known to have no non-periodic face within one step.
+template <class L, bool INT = false>
 __device__ __forceinline__ long long read_slot(const StepArgs &a, const Geo &g, int q, int parity, int &plane_q) {
   if (parity == 0) {
     plane_q = q;
     return g.node;
   }
-  if (crosses<L>(g, q, -1)) {
+  if (!INT && crosses<L>(g, q, -1)) {
     plane_q = q;
     return g.node;
   }
@@ -343,8 +344,9 @@ __device__ __forceinline__ const S *scheme_base(const StepArgs &a, int s) {
   return (const S *)a.pop + (long long)(s * L::Q) * a.plane;
 }
 
-// Load all populations of the node (deviations) with the AA read rule.
-template <class L, class S, class R, bool BS = false, class OffT = long long>
+// Load all populations of the node (deviations) with the AA read rule (INT:
+// an interior node, see read_slot).
+template <class L, class S, class R, bool BS = false, class OffT = long long, bool INT = false>
 __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, R f[6][L::Q]) {
   // the scheme bases formed once, before the loads (left inside the loop
   // they cost the D2Q9 FP32 step 90 instead of 78 us on the 512 x 2048 box)
@@ -354,7 +356,7 @@ __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int p
 #pragma unroll
   for (int q = 0; q < L::Q; q++) {
     int pq;
-    const long long idx = read_slot<L>(a, g, q, parity, pq);
+    const long long idx = read_slot<L, INT>(a, g, q, parity, pq);
     const OffT off = pop_offset<L, OffT>(a, pq, idx);
 #pragma unroll
     for (int s = 0; s < (BS ? 4 : 6); s++) f[s][q] = Store<S>::template ld<R>(sb[s] + off);
@@ -502,9 +504,14 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   R f[6][Q];
   Moments<L, R> m;
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
+  // interior: no non-periodic face within one step of the node (most nodes;
+  // their loads and stores are compiled without the face rules)
+  bool interior = false;
   if (active) {
     make_geo(a, D, g);
-    load_node<L, S, R, BS, OffT>(a, g, parity, f);
+    interior = !(g.xp[0] || g.xm[0] || g.xp[1] || g.xm[1] || g.xp[2] || g.xm[2]);
+    if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f);
+    else load_node<L, S, R, BS, OffT>(a, g, parity, f);
     moments<L, R>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -646,10 +653,12 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   const R eL_gq = Spp_g * P.psi_g, eL_lq = Spp_l * P.psi_l;
   const R c2g = BS ? R(0) : beta_c2<L, R>(cg), c2l = BS ? R(0) : beta_c2<L, R>(cl);
 
-  // face rules of direction q (walls, Tables 1-2) and its AA store
-  auto finish = [&](const int q, R out[6]) {
+  // face rules of direction q (walls, Tables 1-2) and its AA store; INTc
+  // (std::true_type for interior nodes) compiles them out
+  auto finish = [&](const int q, R out[6], auto INTc) {
+    constexpr bool INT = decltype(INTc)::value;
     const R w = wq<L, R>(q);
-    const bool cross = crosses<L>(g, q, +1);
+    const bool cross = !INT && crosses<L>(g, q, +1);
     if (cross) {
       const int rule = face_rule<L>(a, g, q);
       const int qo = L::opp(q);
@@ -714,6 +723,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   // Collisions, direction by direction: the rest direction alone, the moving
   // ones in pairs (q, opp q), whose equilibria share their even part
   // w_q (...) and differ in the sign of their odd part a_q v_q . u.
+  auto collide_all = [&](auto INTc) {
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const int qo = L::opp(q);
@@ -727,7 +737,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
       out[2] = f[2][0] + om_a * (feqS_dv<L, R>(0, aeq_g, deq_g, m.ug, ug2) - f[2][0]);
       out[3] = f[3][0] + om_a * (feqS_dv<L, R>(0, aeq_l, deq_l, m.ul, ul2) - f[3][0]);
       if (!BS) beta_pair<L, R>(0, cg, cl, out[4], out[5]);
-      finish(0, out);
+      finish(0, out, INTc);
     } else if (q < qo) {
       const R w = wq<L, R>(q), aw = aq<L, R>(q);
       const R vug = vdot<L, R>(q, m.ug), vul = vdot<L, R>(q, m.ul);
@@ -757,10 +767,13 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         oa[5] = Rn<R>::fma(aw, vcl, xl);
         ob[5] = Rn<R>::fma(aw, -vcl, xl);
       }
-      finish(q, oa);
-      finish(qo, ob);
+      finish(q, oa, INTc);
+      finish(qo, ob, INTc);
     }
   }
+  };
+  if (interior) collide_all(std::true_type{});
+  else collide_all(std::false_type{});
 }
 
 template <class L, class S, class R, bool BS, class OffT>
