@@ -504,12 +504,17 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   R f[6][Q];
   Moments<L, R> m;
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
-  // interior: no non-periodic face within one step of the node (most nodes;
-  // their loads and stores are compiled without the face rules)
+  // interior: no non-periodic face within one step of any node of the warp
+  // (most warps; their loads and stores are compiled without the face
+  // rules).  Decided per warp, so that a warp holding face nodes takes the
+  // general path whole instead of running both.
   bool interior = false;
   if (active) {
     make_geo(a, D, g);
     interior = !(g.xp[0] || g.xm[0] || g.xp[1] || g.xm[1] || g.xp[2] || g.xm[2]);
+  }
+  interior = __all_sync(__activemask(), interior);
+  if (active) {
     if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f);
     else load_node<L, S, R, BS, OffT>(a, g, parity, f);
     moments<L, R>(a, f, m);
