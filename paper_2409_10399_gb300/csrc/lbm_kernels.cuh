@@ -496,7 +496,7 @@ template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads
 // blk_xch the block exchanges the edge rows' values for the inlet/outlet
 // rules through `xch` and synchronises once, so every thread of the block
 // must call this function.
-template <class L, class S, class R, bool BS = false, class OffT = long long, bool ISPLIT = true>
+template <class L, class S, class R, bool BS = false, class OffT = long long>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
                                                 int latch, bool blk_xch, int gstride, R *xch) {
   constexpr int D = L::D, Q = L::Q;
@@ -509,9 +509,8 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   // rules).  Decided per warp, so that a warp holding face nodes takes the
   // general path whole instead of running both.  Not for the D3Q19 half
   // store: its kernel, twice as long with the second path, ran 12 % slower
-  // on the 3D column (instruction fetch), where the FP32 one gained 5 %; nor
-  // for the batched kernel (ISPLIT false), 0.5 % slower with it.
-  constexpr bool SPLIT = ISPLIT && !(Q == 19 && sizeof(S) == 2);
+  // on the 3D column (instruction fetch), where the FP32 one gained 5 %.
+  constexpr bool SPLIT = !(Q == 19 && sizeof(S) == 2);
   bool interior = false;
   if (active) {
     make_geo(a, D, g);
@@ -842,7 +841,7 @@ __global__ void __launch_bounds__(BatchBounds<L, S>::threads, BatchBounds<L, S>:
   g.c[1] = wi.y0 + threadIdx.y;
   g.c[2] = wi.z0 + threadIdx.z;
   const bool active = g.c[0] < a.n[0] && g.c[1] < a.n[1] && g.c[2] < a.n[2];
-  fused_step_node<L, S, R, false, OffT, false>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
+  fused_step_node<L, S, R, false, OffT>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
 }
 
 // --------------------------------------------------- moments / diagnostics
