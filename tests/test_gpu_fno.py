@@ -171,11 +171,11 @@ def test_adam_step_is_the_textbook_update():
     assert np.abs(m.grads()).max() == 0.0  # zeroed after the step
 
 
-def _lattice(dims=DIMS, seed=5):
+def _lattice(dims=DIMS, seed=5, prec="fp64"):
     import lbm_inputs
     from paper_2409_10399_gb300 import surrogate as S
     nx, ny = dims[0], dims[1]
-    sim = lbm.Simulation("D2Q9", (nx, ny), S._lbm_params("fp64"))
+    sim = lbm.Simulation("D2Q9", (nx, ny), S._lbm_params(prec))
     sim.init(**lbm_inputs.fields_plumes(nx, ny, seed))
     return sim
 
@@ -200,6 +200,28 @@ def test_surrogate_window_on_a_lattice_takes_the_model_state():
     twin = _lattice()
     twin.init(alpha_g=pred[0], u_g=pred[1:3], u_l=pred[3:5], p_k=pred[5])
     assert np.array_equal(_state_of(sim), _state_of(twin))
+
+
+def test_surrogate_window_on_an_fp32_lattice():
+    # the workload's store: deviations from a reference set to the predicted
+    # mean alpha_g, summed on the device by the window and on the host by
+    # lbm_init, so the twin agrees to FP32 rounding rather than bit for bit
+    p, _, _, norm = _case(seed=17)
+    m = _model(p, norm)
+    sim = _lattice(prec="fp32")
+    now = _state_of(sim)
+    _, used = m.advance_lattice(sim, 64, max_drift=1e30)
+    assert used and sim.t == 64
+    pred = torch.empty((6, now.shape[1]), dtype=torch.float64, device="cuda")
+    m.advance(torch.from_numpy(now).cuda().contiguous(), pred, max_drift=1e30)
+    pred = pred.cpu().numpy()
+    twin = _lattice(prec="fp32")
+    twin.init(alpha_g=pred[0], u_g=pred[1:3], u_l=pred[3:5], p_k=pred[5])
+    a, b = _state_of(sim), _state_of(twin)
+    assert np.abs(a[0] - b[0]).max() <= 1e-6 * np.abs(b[0]).max()
+    assert _rel(a[1:5], b[1:5]) < 1e-5
+    sim.step(64)  # the lattice carries on from the re-initialised state
+    assert np.isfinite(_state_of(sim)).all() and sim.t == 128
 
 
 def test_surrogate_window_falls_back_to_the_lattice_steps():
