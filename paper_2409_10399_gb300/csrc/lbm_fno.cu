@@ -185,13 +185,69 @@ __global__ void k_pack_target(const double *now, const double *next, float *t, l
   t[i] = (float)(next[i] - now[i]) * nm.inv_out[c];
 }
 
-// next = now + std_out * y (FP64 state, FP32 increment)
-__global__ void k_unpack(const double *now, const float *y, double *next, long long P, Norm nm) {
-  const int c = blockIdx.y;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+
+// Inference ends of the model, each one pass over the nodes (two per thread)
+// instead of a tensor-core product on mostly padded tiles.  Their numerics
+// are the products': BF16 inputs and weights, FP32 sums, bias added last.
+
+// h_0[c][p] = sum_j W_in[c][j] x_j[p] + b_in[c] from the FP64 state, with
+// x_j the standardised state channel j rounded to BF16 (as k_pack_state)
+// and only the 6 state columns of W_in (the padding inputs are zero)
+__global__ void k_lift(const double *state, const bf16 *W16, int cin, const float *bias, bf16 *h, int C, long long P,
+                       Norm nm) {
+  extern __shared__ float sw[];  // [C][6] weights, then [C] biases
+  for (int i = threadIdx.x; i < C * 6; i += blockDim.x) sw[i] = __bfloat162float(W16[(i / 6) * cin + i % 6]);
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sw[C * 6 + i] = bias[i];
+  __syncthreads();
+  const long long p = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (p >= P) return;
-  const long long i = c * P + p;
-  next[i] = now[i] + (double)nm.std_out[c] * (double)y[i];
+  float x0[6], x1[6];
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    const double m = (double)nm.mean[j];
+    x0[j] = __bfloat162float(__float2bfloat16((float)(state[j * P + p] - m) * nm.inv_in[j]));
+    x1[j] = __bfloat162float(__float2bfloat16((float)(state[j * P + p + 1] - m) * nm.inv_in[j]));
+  }
+  for (int c = 0; c < C; c++) {
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      a0 = fmaf(sw[c * 6 + j], x0[j], a0);
+      a1 = fmaf(sw[c * 6 + j], x1[j], a1);
+    }
+    const float b = sw[C * 6 + c];
+    *reinterpret_cast<__nv_bfloat162 *>(h + c * P + p) = __floats2bfloat162_rn(a0 + b, a1 + b);
+  }
+}
+
+// next[c][p] = now[c][p] + std_out[c] (sum_k W_out[c][k] h_L[k][p] + b_out[c])
+// for the 6 state channels (the padding outputs are not needed)
+__global__ void k_project_out(const bf16 *hL, const bf16 *W16, const float *bias, const double *now, double *next,
+                              int C, long long P, Norm nm) {
+  extern __shared__ float sw[];  // [6][C] weights, then [6] biases
+  for (int i = threadIdx.x; i < 6 * C; i += blockDim.x) sw[i] = __bfloat162float(W16[i]);
+  if (threadIdx.x < 6) sw[6 * C + threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const long long p = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (p >= P) return;
+  float a0[6], a1[6];
+#pragma unroll
+  for (int c = 0; c < 6; c++) a0[c] = a1[c] = 0.0f;
+  for (int k = 0; k < C; k++) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(hL + k * P + p));
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      a0[c] = fmaf(sw[c * C + k], v.x, a0[c]);
+      a1[c] = fmaf(sw[c * C + k], v.y, a1[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    const double s = (double)nm.std_out[c];
+    const float b = sw[6 * C + c];
+    next[c * P + p] = now[c * P + p] + s * (double)(a0[c] + b);
+    next[c * P + p + 1] = now[c * P + p + 1] + s * (double)(a1[c] + b);
+  }
 }
 
 // FP64 sums for the checks of a call, block partials in
@@ -327,17 +383,12 @@ static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z,
   return LBM_OK;
 }
 
-// forward from f->x16 to f->y (cout x P float); keeps h_l, Hx_l, Hy_l, and
-// the pre-activations z_l when `train` (the backward pass needs GELU'(z_l))
-static int forward(lbm_fno *f, bool train) {
+// the L layers, from h_0 to h_L; keeps Hx_l, Hy_l, and the pre-activations
+// z_l when `train` (the backward pass needs GELU'(z_l))
+static int layers(lbm_fno *f, bool train) {
   const int C = f->C, L = f->L;
   const long long P = f->P, CP = (long long)C * P;
   const long long hx = 2LL * f->K * C * f->ny, hy = 2LL * f->K * C * f->nx, wf = (long long)f->K * 4 * C * C;
-  G a;  // lifting: h_0 = W_in x + b_in, stored as bf16 only
-  a.A = f->W_in16; a.lda = f->cin; a.B = f->x16; a.ldb = (int)P; a.C = nullptr; a.ldc = (int)P;
-  a.M = C; a.N = (int)P; a.K = f->cin;
-  a.bias = f->p + f->off.b_in; a.bias_rows = true; a.act = false; a.hout = f->h16;
-  GTRY(f, a);
   for (int l = 0; l < L; l++) {
     const bf16 *h = f->h16 + l * CP;
     float *z = f->z + l * CP;
@@ -346,6 +397,21 @@ static int forward(lbm_fno *f, bool train) {
     rc = spec_y(f, h, f->Hy16 + l * hy, f->Wfy16 + l * wf, z, f->p + f->off.b[l], f->h16 + (l + 1) * CP, train);
     if (rc) return rc;
   }
+  return LBM_OK;
+}
+
+// training forward from f->x16 to f->y (cout x P float): lifting product,
+// layers, output product
+static int forward_train(lbm_fno *f) {
+  const int C = f->C, L = f->L;
+  const long long P = f->P, CP = (long long)C * P;
+  G a;  // lifting: h_0 = W_in x + b_in, stored as bf16 only
+  a.A = f->W_in16; a.lda = f->cin; a.B = f->x16; a.ldb = (int)P; a.C = nullptr; a.ldc = (int)P;
+  a.M = C; a.N = (int)P; a.K = f->cin;
+  a.bias = f->p + f->off.b_in; a.bias_rows = true; a.act = false; a.hout = f->h16;
+  GTRY(f, a);
+  int rc = layers(f, true);
+  if (rc) return rc;
   G o;  // y = W_out h_L + b_out
   o.A = f->W_out16; o.lda = C; o.B = f->h16 + L * CP; o.ldb = (int)P; o.C = f->y; o.ldc = (int)P;
   o.M = f->cout; o.N = (int)P; o.K = C;
@@ -688,7 +754,7 @@ int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double
   k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
   k_pack_target<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, next, f->tgt, P, nm);
   f->launches += 2;
-  int rc = forward(f, true);
+  int rc = forward_train(f);
   if (rc) return rc;
   return backward(f, loss);
 }
@@ -728,11 +794,14 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   if (!f || !now || !next || now == next) return LBM_EINVAL;
   const long long P = f->P;
   const Norm nm = norm_of(f);
-  k_pack_state<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->x16, P, nm);
+  const int C = f->C;
+  k_lift<<<nblk(P / 2), 256, (size_t)C * 7 * sizeof(float), f->stream>>>(now, f->W_in16, f->cin,
+                                                                         f->p + f->off.b_in, f->h16, C, P, nm);
   f->launches++;
-  int rc = forward(f, false);
+  int rc = layers(f, false);
   if (rc) return rc;
-  k_unpack<<<dim3(nblk(P), 6), 256, 0, f->stream>>>(now, f->y, next, P, nm);
+  k_project_out<<<nblk(P / 2), 256, (size_t)(6 * C + 6) * sizeof(float), f->stream>>>(
+      f->h16 + (long long)f->L * C * P, f->W_out16, f->p + f->off.b_out, now, next, C, P, nm);
   f->launches++;
   FTRY(f, cudaGetLastError());
   // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g;
