@@ -292,215 +292,6 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   }
 }
 
-// Streaming form of the product for the surrogate's epilogue-heavy products
-// (float C, ksplit 1; same arguments and results as k_gemm): a grid of
-// resident blocks, each walking the output tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ... with one cp.async ring, so that the next
-// tile's operand slices (and, with PRE, its old output tile) are in flight
-// while the current tile's epilogue runs.  The output tile has a shared
-// buffer of its own (46.6 KB of shared memory a block: 4 blocks per SM).  Tiles are numbered (batch, row block, column block),
-// column block fastest; tn, tm: column and row blocks.
-template <bool TA, bool TB, bool SEG2, bool PRE>
-__global__ void __launch_bounds__(128, 4) k_gemm_stream(const GemmArgs g, int tn, int tm, int ntiles) {
-  using namespace nvcuda;
-  typedef GemmSmem<TA, TB> SM;
-  constexpr int A_ROWS = SM::A_ROWS, A_COLS = SM::A_COLS, B_ROWS = SM::B_ROWS, B_COLS = SM::B_COLS;
-  constexpr int A_LD = SM::A_LD, B_LD = SM::B_LD;
-  constexpr int PER = GBM * GBN / 4 / 128;
-  __shared__ __align__(128) unsigned char smem[SM::PIPE];
-  __shared__ __align__(32) float sC[GBM][GBN + 4];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int nk1 = (g.K + GBK - 1) / GBK;
-  const int S = nk1 + (SEG2 ? (g.K2 + GBK - 1) / GBK : 0);
-  const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int total = mine * S;
-
-  auto tile_of = [&](int i, int &b, int &m0, int &n0) {
-    const int t = (int)blockIdx.x + i * (int)gridDim.x;
-    b = t / (tn * tm);
-    const int r = t % (tn * tm);
-    m0 = (r / tn) * GBM;
-    n0 = (r % tn) * GBN;
-  };
-  // k-slice s of this block's tile gsl / S into ring slot st, zero outside the matrices
-  auto load_slice = [&](int st, int gsl) {
-    int b, m0, n0;
-    tile_of(gsl / S, b, m0, n0);
-    const int s = gsl % S;
-    unsigned char *slot = smem + st * SM::STAGE;
-    if (!SEG2 || s < nk1) {
-      const bf16 *A = g.A + (long long)b * g.sA, *B = g.B + (long long)b * g.sB;
-      const int k0 = s * GBK;
-      bf16 *sA = reinterpret_cast<bf16 *>(slot), *sB = reinterpret_cast<bf16 *>(slot + SM::A_BYTES);
-#pragma unroll
-      for (int v = tid; v < A_ROWS * A_COLS / 8; v += 128) {
-        const int r = v / (A_COLS / 8), c = (v % (A_COLS / 8)) * 8;
-        const int gr = (TA ? k0 : m0) + r, gc = (TA ? m0 : k0) + c;
-        const int mi = TA ? gc : gr, ki = TA ? gr : gc;
-        const bool ok = mi < g.M && ki < g.K;
-        cp_async16(sA + r * A_LD + c, ok ? A + (long long)gr * g.lda + gc : A, ok);
-      }
-#pragma unroll
-      for (int v = tid; v < B_ROWS * B_COLS / 8; v += 128) {
-        const int r = v / (B_COLS / 8), c = (v % (B_COLS / 8)) * 8;
-        const int gr = (TB ? n0 : k0) + r, gc = (TB ? k0 : n0) + c;
-        const int ni = TB ? gr : gc, ki = TB ? gc : gr;
-        const bool ok = ni < g.N && ki < g.K;
-        cp_async16(sB + r * B_LD + c, ok ? B + (long long)gr * g.ldb + gc : B, ok);
-      }
-    } else {
-      const bf16 *A2 = g.A2 + (long long)(n0 / g.seg_nx) * g.a2_rs;
-      const bf16 *B2 = g.B2 + (long long)(n0 % g.seg_nx) * g.ldb2;
-      const int k0 = (s - nk1) * GBK;
-      bf16 *sA2 = reinterpret_cast<bf16 *>(slot), *sB2 = reinterpret_cast<bf16 *>(slot + SM::A2_BYTES);
-#pragma unroll
-      for (int v = tid; v < GBK * GBM / 8; v += 128) {
-        const int r = v / (GBM / 8), c = (v % (GBM / 8)) * 8, ki = k0 + r, mi = m0 + c;
-        const bool ok = mi < g.M && ki < g.K2;
-        cp_async16(sA2 + r * SM::A2_LD + c, ok ? A2 + (long long)ki * g.lda2 + mi : A2, ok);
-      }
-#pragma unroll
-      for (int v = tid; v < GBN * GBK / 8; v += 128) {
-        const int r = v / (GBK / 8), c = (v % (GBK / 8)) * 8, ni = n0 + r, ki = k0 + c;
-        const bool ok = ni < g.N && ki < g.K2;
-        cp_async16(sB2 + r * SM::B2_LD + c, ok ? B2 + (long long)r * g.ldb2 + ki : B2, ok);
-      }
-    }
-  };
-  float4 pre[PRE ? PER : 1];
-  auto prefetch_c = [&](int i) {
-    int b, m0, n0;
-    tile_of(i, b, m0, n0);
-    const float *Cb = reinterpret_cast<const float *>(g.C) + (long long)b * g.sC;
-#pragma unroll
-    for (int j = 0; j < PER; j++) {
-      const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
-      pre[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < g.M && gc < g.N) pre[j] = *reinterpret_cast<const float4 *>(Cb + (long long)gr * g.ldc + gc);
-    }
-  };
-  if constexpr (PRE) {
-    if (mine > 0) prefetch_c(0);
-  }
-
-  typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16,
-                         typename std::conditional<TA, wmma::col_major, wmma::row_major>::type> FragA;
-  typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16,
-                         typename std::conditional<TB, wmma::col_major, wmma::row_major>::type> FragB;
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
-
-#pragma unroll
-  for (int st = 0; st < GSTAGES - 1; st++) {
-    if (st < total) load_slice(st, st);
-    cp_async_commit();
-  }
-  for (int gs = 0; gs < total; gs++) {
-    cp_async_wait<GSTAGES - 2>();  // slice gs has landed (this thread's copies)
-    __syncthreads();               // ... everyone's; slot (gs - 1) % GSTAGES is free
-    if (gs + GSTAGES - 1 < total) load_slice((gs + GSTAGES - 1) % GSTAGES, gs + GSTAGES - 1);
-    cp_async_commit();
-    const int s = gs % S;
-    if (s == 0) {
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 2; j++) wmma::fill_fragment(acc[i][j], 0.0f);
-    }
-    const unsigned char *slot = smem + (gs % GSTAGES) * SM::STAGE;
-    if (!SEG2 || s < nk1) {
-      const bf16 *sA = reinterpret_cast<const bf16 *>(slot);
-      const bf16 *sB = reinterpret_cast<const bf16 *>(slot + SM::A_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < GBK; kk += 16) {
-        FragA fa[2];
-        FragB fb[2];
-#pragma unroll
-        for (int i = 0; i < 2; i++) {
-          const bf16 *pa = TA ? sA + kk * A_LD + wm + 16 * i : sA + (wm + 16 * i) * A_LD + kk;
-          wmma::load_matrix_sync(fa[i], pa, A_LD);
-          const bf16 *pb = TB ? sB + (wn + 16 * i) * B_LD + kk : sB + kk * B_LD + wn + 16 * i;
-          wmma::load_matrix_sync(fb[i], pb, B_LD);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-          for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-      }
-    } else if constexpr (SEG2) {
-      typedef wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::col_major> FragA2;
-      typedef wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::col_major> FragB2;
-      const bf16 *sA2 = reinterpret_cast<const bf16 *>(slot);
-      const bf16 *sB2 = reinterpret_cast<const bf16 *>(slot + SM::A2_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < GBK; kk += 16) {
-        FragA2 fa[2];
-        FragB2 fb[2];
-#pragma unroll
-        for (int i = 0; i < 2; i++) {
-          wmma::load_matrix_sync(fa[i], sA2 + kk * SM::A2_LD + wm + 16 * i, SM::A2_LD);
-          wmma::load_matrix_sync(fb[i], sB2 + (wn + 16 * i) * SM::B2_LD + kk, SM::B2_LD);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-          for (int j = 0; j < 2; j++) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-      }
-    }
-    if (s == S - 1) {
-      // the tile is complete: epilogue while the next tile's slices arrive.
-      // sC is rewritten only at the next tile's end, behind at least one
-      // barrier at the top of the loop.
-      const int ti = gs / S;
-      int b, m0, n0;
-      tile_of(ti, b, m0, n0);
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 2; j++)
-          wmma::store_matrix_sync(&sC[wm + 16 * i][wn + 16 * j], acc[i][j], GBN + 4, wmma::mem_row_major);
-      __syncthreads();
-      float *C = reinterpret_cast<float *>(g.C) + (long long)b * g.sC;
-      float4 old[PER];
-#pragma unroll
-      for (int j = 0; j < PER; j++) {
-        const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
-        old[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (PRE) {
-          old[j] = pre[j];
-        } else if (g.beta != 0.0f && gr < g.M && gc < g.N) {
-          old[j] = *reinterpret_cast<const float4 *>(C + (long long)gr * g.ldc + gc);
-        }
-      }
-      if constexpr (PRE) {
-        if (ti + 1 < mine) prefetch_c(ti + 1);  // the next tile's old C, behind this epilogue
-      }
-#pragma unroll
-      for (int j = 0; j < PER; j++) {
-        const int v = tid + j * 128, r = v / (GBN / 4), c = (v % (GBN / 4)) * 4, gr = m0 + r, gc = n0 + c;
-        if (gr >= g.M || gc >= g.N) continue;
-        float o[4] = {g.alpha * sC[r][c] + g.beta * old[j].x, g.alpha * sC[r][c + 1] + g.beta * old[j].y,
-                      g.alpha * sC[r][c + 2] + g.beta * old[j].z, g.alpha * sC[r][c + 3] + g.beta * old[j].w};
-        if (g.bias) {
-          const float bb = g.bias_rows ? g.bias[gr] : g.bias[b];
-#pragma unroll
-          for (int e = 0; e < 4; e++) o[e] += bb;
-        }
-        if (g.hout) {
-          bf16 hv[4];
-#pragma unroll
-          for (int e = 0; e < 4; e++) hv[e] = __float2bfloat16(g.act ? gelu(o[e]) : o[e]);
-          *reinterpret_cast<uint2 *>(g.hout + (long long)b * g.sC + (long long)gr * g.ldc + gc) =
-              *reinterpret_cast<const uint2 *>(hv);
-        }
-        if (g.C && g.store_c)
-          *reinterpret_cast<float4 *>(C + (long long)gr * g.ldc + gc) = make_float4(o[0], o[1], o[2], o[3]);
-      }
-    }
-  }
-  cp_async_wait<0>();
-}
-
 // ---------------------------------------------------------------- elementwise
 
 // hardware tanh (PTX tanh.approx.f32, relative error ~2^-11): below the

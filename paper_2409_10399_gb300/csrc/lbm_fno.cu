@@ -117,30 +117,11 @@ struct G {
   const bf16 *A2 = nullptr, *B2 = nullptr;
   int K2 = 0, lda2 = 0, ldb2 = 0, seg_nx = 0;
   long long a2_rs = 0;
-  bool stream = false;  // fno::k_gemm_stream: resident blocks walking the tiles (float C, ksplit 1)
 };
 
 template <bool TA, bool TB, class OutT, bool SEG2 = false, bool PRE = false>
 static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
   fno::k_gemm<TA, TB, OutT, SEG2, PRE><<<grid, 128, 0, st>>>(a);
-}
-
-// the streaming form on as many blocks as are resident at once (at most one
-// per tile); the occupancy is asked once per instance
-template <bool TA, bool TB, bool SEG2, bool PRE>
-static cudaError_t launch_stream_t(const fno::GemmArgs &a, int tn, int tm, int ntiles, cudaStream_t st) {
-  static int resident = 0;
-  if (!resident) {
-    int dev = 0, sms = 0, per = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fno::k_gemm_stream<TA, TB, SEG2, PRE>, 128, 0);
-    if (e != cudaSuccess) return e;
-    resident = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
-  }
-  const int grid = ntiles < resident ? ntiles : resident;
-  fno::k_gemm_stream<TA, TB, SEG2, PRE><<<grid, 128, 0, st>>>(a, tn, tm, ntiles);
-  return cudaSuccess;
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
@@ -165,18 +146,6 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
                   g.A2, g.B2, g.K2, g.lda2, g.ldb2, g.seg_nx, g.a2_rs};
   dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
   const bool pre = g.out_f32 && g.beta != 0.0f && ks == 1;  // accumulate into C: prefetch the old tile
-  if (g.stream) {
-    if (!g.out_f32 || ks != 1 || !g.C || g.ta || g.tb) return cudaErrorInvalidValue;
-    const int tn = (g.N + fno::GBN - 1) / fno::GBN, tm = (g.M + fno::GBM - 1) / fno::GBM;
-    const long long nt = (long long)tn * tm * g.batch;
-    if (nt > (1LL << 30)) return cudaErrorInvalidValue;
-    cudaError_t e;
-    if (g.A2) e = launch_stream_t<false, false, true, false>(a, tn, tm, (int)nt, st);
-    else if (pre) e = launch_stream_t<false, false, false, true>(a, tn, tm, (int)nt, st);
-    else e = launch_stream_t<false, false, false, false>(a, tn, tm, (int)nt, st);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-  }
   if (g.A2) launch_gemm_t<false, false, float, true>(a, grid, st);
   else if (pre && g.ta && g.tb) launch_gemm_t<true, true, float, false, true>(a, grid, st);
   else if (pre && g.ta) launch_gemm_t<true, false, float, false, true>(a, grid, st);
@@ -358,7 +327,6 @@ static int pointwise_and_spec_x(lbm_fno *f, const bf16 *W, const bf16 *h, bf16 *
     // ... + for the tile of row y: O[y]^T (C x 2K) B_xi^T (2K x columns)
     w.A2 = f->O16; w.lda2 = C; w.a2_rs = (long long)K2 * C;
     w.B2 = f->Bxi; w.ldb2 = K2; w.K2 = K2; w.seg_nx = nx;
-    w.stream = true;
     GTRY(f, w);
     return LBM_OK;
   }
@@ -411,7 +379,6 @@ static int spec_y(lbm_fno *f, const bf16 *h, bf16 *Hy, const bf16 *Wf, float *z,
   c.C = z; c.ldc = nx; c.sC = P; c.beta = 1.0f;
   c.M = ny; c.N = nx; c.K = K2; c.batch = C;
   c.bias = bias; c.hout = hnext; c.store_c = keep_z;
-  c.stream = true;
   GTRY(f, c);
   return LBM_OK;
 }
