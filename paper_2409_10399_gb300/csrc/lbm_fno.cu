@@ -233,8 +233,6 @@ __global__ void k_project_out(const bf16 *hL, const bf16 *W16, const float *bias
   float a0[6], a1[6];
 #pragma unroll
   for (int c = 0; c < 6; c++) a0[c] = a1[c] = 0.0f;
-  // unrolled so that several channel planes are loaded at once (C is a multiple of 16)
-#pragma unroll 8
   for (int k = 0; k < C; k++) {
     const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(hL + k * P + p));
 #pragma unroll
@@ -261,8 +259,6 @@ __global__ void k_checks(const double *a0, const double *a1, long long n, double
   const double *a = blockIdx.y == 0 ? a0 : a1;
   const long long m = blockIdx.y == 2 ? 6 * n : n;
   double acc = 0.0;
-  // unrolled so that several loads of the grid-stride loop are in flight at once
-#pragma unroll 4
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
     const double v = a[i];
     acc += blockIdx.y == 3 ? (v >= 0.0 && v <= 1.0 ? 0.0 : 1.0) : v;
