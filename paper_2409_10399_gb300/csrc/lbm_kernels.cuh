@@ -496,7 +496,9 @@ template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads
 // blk_xch the block exchanges the edge rows' values for the inlet/outlet
 // rules through `xch` and synchronises once, so every thread of the block
 // must call this function.
-template <class L, class S, class R, bool BS = false, class OffT = long long>
+// IO false: the lattice has no inlet or outlet face (walls and periodic axes
+// only), and the inlet/outlet rules are compiled out.
+template <class L, class S, class R, bool BS = false, class OffT = long long, bool IO = true>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
                                                 int latch, bool blk_xch, int gstride, R *xch) {
   constexpr int D = L::D, Q = L::Q;
@@ -537,7 +539,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
       cw[(D + d) * a.plane + g.node] = (H)cl[d];
     }
   }
-  if (blk_xch) {
+  if (IO && blk_xch) {
     if (active) {
 #pragma unroll
       for (int d = 0; d < 3; d++) {
@@ -667,7 +669,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
     constexpr bool INT = decltype(INTc)::value;
     const R w = wq<L, R>(q);
     const bool cross = !INT && crosses<L>(g, q, +1);
-    if (cross) {
+    if (IO && cross) {
       const int rule = face_rule<L>(a, g, q);
       const int qo = L::opp(q);
       if (rule == BC_INLET) {
@@ -784,7 +786,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   else collide_all(std::false_type{});
 }
 
-template <class L, class S, class R, bool BS, class OffT>
+template <class L, class S, class R, bool BS, class OffT, bool IO = true>
 __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::blocks) k_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *xch = reinterpret_cast<R *>(smem_raw);
@@ -802,8 +804,8 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   const int ng = gax == 0 ? a.n[0] : (gax == 1 ? a.n[1] : a.n[2]);
   const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
-  const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
-  fused_step_node<L, S, R, BS, OffT>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
+  const bool blk_xch = IO && ((a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng));
+  fused_step_node<L, S, R, BS, OffT, IO>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
 }
 
 // Batched form: one launch advances many independent lattices (instances) of

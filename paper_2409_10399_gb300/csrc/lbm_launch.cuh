@@ -16,8 +16,14 @@ struct Launch {
   // in both forms
   template <bool BS, class OffT>
   static void step_form(int prec, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    // the fast six-scheme forms also come without the inlet/outlet rules,
+    // for lattices with walls and periodic axes only (a smaller kernel)
+    constexpr bool WO = !BS && std::is_same<OffT, unsigned>::value;
+    const bool io = a.has_inlet || a.has_outlet;
     if (prec == 3) k_step<L, double, double, BS, OffT><<<grid, block, smem, st>>>(a);
+    else if (prec == 1 && WO && !io) k_step<L, float, float, BS, OffT, false><<<grid, block, smem, st>>>(a);
     else if (prec == 1) k_step<L, float, float, BS, OffT><<<grid, block, smem, st>>>(a);
+    else if (WO && !io) k_step<L, __half, float, BS, OffT, false><<<grid, block, smem, st>>>(a);
     else k_step<L, __half, float, BS, OffT><<<grid, block, smem, st>>>(a);
   }
   // six-scheme store: 32-bit population offsets where they fit; the
