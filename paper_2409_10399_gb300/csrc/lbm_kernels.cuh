@@ -843,7 +843,8 @@ __global__ void __launch_bounds__(BatchBounds<L, S>::threads, BatchBounds<L, S>:
   g.c[1] = wi.y0 + threadIdx.y;
   g.c[2] = wi.z0 + threadIdx.z;
   const bool active = g.c[0] < a.n[0] && g.c[1] < a.n[1] && g.c[2] < a.n[2];
-  fused_step_node<L, S, R, false, OffT>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
+  // no inlet or outlet rules: lbm_batch_create accepts walls and periodic axes only
+  fused_step_node<L, S, R, false, OffT, false>(a, g, active, 0, parity, latch, false, 0, (R *)nullptr);
 }
 
 // --------------------------------------------------- moments / diagnostics
