@@ -11,9 +11,11 @@
 // k < K, interleaved), per mode the complex channel mixing
 // [O_c; O_s] = [[A_k, -B_k], [B_k, A_k]] [H_c; H_s], back with the inverse
 // basis (B_x scaled by 1/n_x for k = 0, 2/n_x otherwise).  S^y likewise
-// along y.  Every contraction is a BF16 matrix product with FP32
-// accumulation (fno_kernels.cuh); activations of the backward pass are kept
-// per layer (z in FP32, h and the spectral coefficients in BF16).
+// along y.  Every contraction of the layers is a BF16 matrix product with
+// FP32 accumulation (fno_kernels.cuh); the lifting and output projection are
+// products too in training, and direct passes over the nodes with the same
+// numerics in inference (lbm_fno_advance).  Activations of the backward pass
+// are kept per layer (z in FP32, h and the spectral coefficients in BF16).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
