@@ -80,6 +80,11 @@ struct lbm_fno {
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t stream = 0;
   long long launches = 0;
+  // the inference layers as a CUDA graph, captured at the first call (all
+  // their buffers belong to the model) and replayed on the model's stream
+  cudaGraphExec_t layers_exec = nullptr;
+  long long layers_launches = 0;  // kernels in one replay
+  bool layers_graph_off = false;  // capture failed: plain launches
   char err[512] = {0};
 };
 
@@ -603,6 +608,7 @@ int lbm_fno_destroy(lbm_fno *f) {
     if (b) cudaFree(b);
   if (f->h_part) cudaFreeHost(f->h_part);
   if (f->h_red) cudaFreeHost(f->h_red);
+  if (f->layers_exec) cudaGraphExecDestroy(f->layers_exec);
   delete f;
   return LBM_OK;
 }
@@ -792,6 +798,50 @@ static int check_sums(lbm_fno *f, const double *now, const double *next, double 
   return LBM_OK;
 }
 
+// The inference layers: replayed from a graph captured on a stream of the
+// model's own (the legacy default stream cannot be captured), else launched.
+static int run_layers_inference(lbm_fno *f) {
+  if (!f->layers_exec && !f->layers_graph_off) {
+    cudaStream_t user = f->stream, cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+      // the capture must not start before earlier work on the user's stream
+      cudaEvent_t ev = nullptr;
+      ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventRecord(ev, user) == cudaSuccess && cudaStreamWaitEvent(cap, ev, 0) == cudaSuccess;
+      if (ev) cudaEventDestroy(ev);
+    }
+    const long long l0 = f->launches;
+    if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = LBM_OK;
+    if (ok) {
+      f->stream = cap;
+      rc = layers(f, false);
+      f->stream = user;
+      ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && rc == LBM_OK;
+    }
+    if (ok) ok = cudaGraphInstantiate(&f->layers_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    f->layers_launches = f->launches - l0;
+    f->launches = l0;
+    if (!ok) {
+      cudaGetLastError();
+      if (f->layers_exec) cudaGraphExecDestroy(f->layers_exec);
+      f->layers_exec = nullptr;
+      f->layers_graph_off = true;
+      f->err[0] = 0;
+    }
+  }
+  if (f->layers_exec) {
+    FTRY(f, cudaGraphLaunch(f->layers_exec, f->stream));
+    f->launches += f->layers_launches;
+    return LBM_OK;
+  }
+  return layers(f, false);
+}
+
 int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok) {
   if (!f || !now || !next || now == next) return LBM_EINVAL;
   const long long P = f->P;
@@ -800,7 +850,7 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
   k_lift<<<nblk(P / 2), 256, (size_t)C * 7 * sizeof(float), f->stream>>>(now, f->W_in16, f->cin,
                                                                          f->p + f->off.b_in, f->h16, C, P, nm);
   f->launches++;
-  int rc = layers(f, false);
+  int rc = run_layers_inference(f);
   if (rc) return rc;
   k_project_out<<<nblk(P / 2), 256, (size_t)(6 * C + 6) * sizeof(float), f->stream>>>(
       f->h16 + (long long)f->L * C * P, f->W_out16, f->p + f->off.b_out, now, next, C, P, nm);
