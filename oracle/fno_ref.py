@@ -20,8 +20,12 @@ mixed by [[A, -B], [B, A]] and summed back as (1/n)(c_0) + (2/n) sum_k
 (c_k cos + s_k sin), the library's form.  GELU is the tanh approximation.
 Loss: mean over the 6 state channels and all nodes of (y - t)^2, plus
 cons * (mean over the nodes of y_0 - t_0)^2 (channel 0 is alpha_g).
-Parity unpinned beyond the finite-difference and identity pins listed in the
-test file (the surrogate is not the paper's method).
+Pinned by tests/test_oracle_fno.py: its gradient against central finite
+differences of its loss (with and without the conservation term), identity
+mixing reproducing band-limited signals and removing modes >= K, the weight i
+turning cos into sin, and the all-zero model's loss and output-bias gradient
+in closed form.  The surrogate is not the paper's method: these pins fix the
+model the library defines, not a result of the paper.
 """
 import math
 
