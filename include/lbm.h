@@ -164,6 +164,16 @@ int lbm_lattice(int lattice, int *Q, int *v, double *w);
  * [4] max |u| over both phases, [5] number of nodes with a non-finite
  * population, [6] sum (eps_g - 1), [7] sum (eps_l - 1).  Synchronises. */
 int lbm_get_diag(lbm_ctx *c, double out[8]);
+/* Graph replay of lbm_step (default on).  When the step arguments repeat
+ * exactly (no inlet ramp in progress; after the beta-stencil form's first
+ * step) with period lcm(2, n_gamma, diag_every) <= 4096, lbm_step replays
+ * whole periods from a CUDA graph captured once on a stream of the library's
+ * own, which removes the launch gaps between steps; the results are bitwise
+ * those of plain launches.  Within a replayed period only its last
+ * diagnostics are read by the host (the FP64 reductions of every diag_every
+ * steps still run).  enable = 0 launches every step.  lbm_init and
+ * lbm_set_tile drop the captured graph.  Not in the paper. */
+int lbm_set_graph(lbm_ctx *c, int enable);
 
 /* Use `cuda_stream` (a cudaStream_t of the current device, e.g. the value of
  * torch.cuda.current_stream().cuda_stream) for all later work; NULL selects

@@ -79,6 +79,7 @@ def load_library(build_if_missing=True):
             "lbm_get_diag": (I, [P, ctypes.POINTER(D)]),
             "lbm_set_stream": (I, [P, P]),
             "lbm_time": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_set_graph": (I, [P, I]),
             "lbm_set_tile": (I, [P, I, I, I]),
             "lbm_get_tile": (I, [P, ctypes.POINTER(I)]),
             "lbm_tile_limit": (I, [I, I, ctypes.POINTER(I)]),
@@ -324,6 +325,10 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    def set_graph(self, enable):
+        """Replay periods of steps from a CUDA graph (lbm_set_graph; default on)."""
+        self._check(self._lib.lbm_set_graph(self._h, 1 if enable else 0), "lbm_set_graph")
 
     def set_stream(self, stream):
         """Use a torch.cuda.Stream (or a raw cudaStream_t int) for all work."""

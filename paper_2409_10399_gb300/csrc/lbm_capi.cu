@@ -331,6 +331,12 @@ cudaError_t launch_batch_step(int lattice, int prec, const StepArgs *args, const
 }
 }  // namespace lbm
 
+static void drop_graph(lbm_ctx *c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_period = 0;
+}
+
 // Equilibrium populations from device fields whose alpha_g (all in [0, 1])
 // sums to alpha_sum: the deviation reference is its mean; clock at 0.
 static int init_fields(lbm_ctx *c, const double *da, const double *dug, const double *dul, const double *dpk,
@@ -338,6 +344,7 @@ static int init_fields(lbm_ctx *c, const double *da, const double *dug, const do
   c->r_ag = alpha_sum / (double)c->N;
   c->r_al = 1.0 - c->r_ag;
   c->t = 0;
+  drop_graph(c);  // the deviation references are step arguments
   MomArgs ma = make_mom(c, nullptr);
   CUDA_TRY(c, dispatch_init(c, ma, da, dug, dul, dpk));
   c->mass0 = alpha_sum;
@@ -527,28 +534,117 @@ static int enqueue_diag(lbm_ctx *c, double *dev_out) {
   return LBM_OK;
 }
 
+// One step: the launch, and the diagnostics every diag_every steps.
+static int one_step(lbm_ctx *c) {
+  StepArgs a = make_args(c, c->t);
+  CUDA_TRY(c, dispatch_step(c, a));
+  c->t++;
+  if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
+    if (c->diag_pending) {
+      int rc = check_diag(c, 1);
+      if (rc) return rc;
+    }
+    int rc = enqueue_diag(c, c->diag_dev);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_diag, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->diag_ev, c->stream));
+    c->diag_pending = 1;
+  }
+  return LBM_OK;
+}
+
+static long long gcd_ll(long long a, long long b) { return b ? gcd_ll(b, a % b) : a; }
+
+// Period after which the step arguments (parity, lag latch, diagnostics)
+// repeat exactly, or 0 when they do not (an inlet ramp still changing them,
+// the beta-stencil form's first step) or the period would be long.
+static int graph_period(const lbm_ctx *c) {
+  if (!c->use_graph) return 0;
+  if (c->p.bc_lo[c->p.g_axis] == LBM_BC_INLET && c->p.ramp_nt > 0) return 0;
+  if (c->cfield && c->t == 0) return 0;
+  long long per = c->p.n_gamma % 2 == 0 ? c->p.n_gamma : 2LL * c->p.n_gamma;
+  if (c->p.diag_every > 0) per = per / gcd_ll(per, c->p.diag_every) * c->p.diag_every;
+  return per <= 4096 ? (int)per : 0;
+}
+
+// One period from the graph, captured at its first use on a stream of the
+// lattice's own (the legacy default stream cannot be captured) and replayed on
+// the lattice's stream.  Only the last diagnostics of a period reach the host.
+static int replay_period(lbm_ctx *c, int period) {
+  if (c->diag_pending) {
+    int rc = check_diag(c, 1);
+    if (rc) return rc;
+  }
+  if (!c->graph || c->graph_period != period) {
+    drop_graph(c);
+    if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t user = c->stream;
+    const long long t0 = c->t, l0 = c->launches;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->cap_stream;
+    int rc = LBM_OK;
+    for (int k = 0; k < period && !rc; k++) {
+      StepArgs a = make_args(c, t0 + k);
+      cudaError_t e = dispatch_step(c, a);
+      if (e != cudaSuccess) rc = set_err(c, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+      if (!rc && c->p.diag_every > 0 && (t0 + k + 1) % c->p.diag_every == 0) {
+        rc = enqueue_diag(c, c->diag_dev);
+        if (!rc && (cudaMemcpyAsync(c->h_diag, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream) != cudaSuccess ||
+                    cudaEventRecord(c->diag_ev, c->stream) != cudaSuccess))
+          rc = set_err(c, LBM_ECUDA, "graph capture of the diagnostics");
+      }
+    }
+    c->stream = user;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    if (!rc && e != cudaSuccess) rc = set_err(c, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (!rc) {
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      if (e != cudaSuccess) rc = set_err(c, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc) {
+      cudaGetLastError();
+      drop_graph(c);
+      return rc;
+    }
+    c->graph_period = period;
+  }
+  CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+  c->launches += c->graph_launches;
+  c->t += period;
+  if (c->p.diag_every > 0) c->diag_pending = 1;
+  return LBM_OK;
+}
+
 int lbm_step(lbm_ctx *c, int n) {
   if (!c || n < 0) return LBM_EINVAL;
   if (!c->initialised) return set_err(c, LBM_ESTATE, "lbm_step before lbm_init");
   if (c->sticky) return set_err(c, LBM_ESTATE, "sticky error %d; call lbm_init", c->sticky);
   int rc = check_diag(c, 0);
   if (rc) return rc;
-  for (int k = 0; k < n; k++) {
-    StepArgs a = make_args(c, c->t);
-    CUDA_TRY(c, dispatch_step(c, a));
-    c->t++;
-    if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
-      if (c->diag_pending) {
-        rc = check_diag(c, 1);
-        if (rc) return rc;
-      }
-      rc = enqueue_diag(c, c->diag_dev);
-      if (rc) return rc;
-      CUDA_TRY(c, cudaMemcpyAsync(c->h_diag, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      CUDA_TRY(c, cudaEventRecord(c->diag_ev, c->stream));
-      c->diag_pending = 1;
+  long long left = n;
+  while (left > 0) {
+    const int period = graph_period(c);
+    if (period > 0 && c->t % period == 0 && left >= period) {
+      rc = replay_period(c, period);
+      left -= period;
+    } else {
+      rc = one_step(c);
+      left--;
     }
+    if (rc) return rc;
   }
+  return LBM_OK;
+}
+
+int lbm_set_graph(lbm_ctx *c, int enable) {
+  if (!c) return LBM_EINVAL;
+  c->use_graph = enable ? 1 : 0;
+  drop_graph(c);
   return LBM_OK;
 }
 
@@ -616,6 +712,7 @@ int lbm_set_tile(lbm_ctx *c, int tx, int ty, int tz) {
     return set_err(c, LBM_EINVAL, "invalid tile %dx%dx%d (at most %d threads, a multiple of 32)", tx, ty, tz,
                    max_tile_threads(c));
   int old[3] = {c->T[0], c->T[1], c->T[2]};
+  drop_graph(c);  // the launch shape is part of the captured launches
   c->T[0] = tx;
   c->T[1] = ty;
   c->T[2] = tz;
@@ -659,6 +756,8 @@ int lbm_destroy(lbm_ctx *c) {
   if (c->h_diag) cudaFreeHost(c->h_diag);
   if (c->diag_ev) cudaEventDestroy(c->diag_ev);
   if (c->stage) cudaFree(c->stage);
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return LBM_OK;
 }

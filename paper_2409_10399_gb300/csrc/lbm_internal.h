@@ -28,6 +28,13 @@ struct lbm_ctx {
   int T[3] = {1, 1, 1}, shift[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
   size_t smem = 0;
   long long launches = 0;
+  // steps replayed from a CUDA graph of one period of the step arguments
+  // (lbm_step; lattices whose arguments repeat: no inlet ramp)
+  int use_graph = 1;
+  cudaGraphExec_t graph = nullptr;
+  int graph_period = 0;
+  long long graph_launches = 0;   // kernels in one replay
+  cudaStream_t cap_stream = nullptr;  // capture stream of the lattice's own
   char err[512] = {0};
 };
 

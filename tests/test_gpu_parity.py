@@ -294,3 +294,32 @@ def test_results_independent_of_tile(prec):
     if prec == "fp32":
         with pytest.raises(lbm.LBMError):
             s.set_tile(64, 4, 1)  # the 2D float kernel is built for at most 128 threads
+
+
+@pytest.mark.parametrize("name,prec,extra", [
+    ("d2q9_walls", "fp32", dict(diag_every=20)),
+    ("d2q9_walls", "fp16dev", dict(diag_every=0)),
+    ("d3q19_walls", "fp32", dict(diag_every=6)),
+    ("d1q3_walls", "fp64", dict(diag_every=35)),
+    ("d2q9_walls", "fp32", dict(beta_stencil=1, diag_every=0)),
+])
+def test_graph_replay_is_bitwise_plain_launches(name, prec, extra):
+    """lbm_step replays periods of lcm(2, n_gamma, diag_every) steps from a CUDA
+    graph when the step arguments repeat (closed lattices): the fields are
+    bitwise those of plain launches, over whole periods and ragged remainders,
+    the diagnostics agree, and the launch count is the same."""
+    lat, dims, p, _ = CASES[name]
+    f = case_fields(lat, dims, seed=9)
+    runs = []
+    for graph in (True, False):
+        s = lbm.Simulation(lat, dims, dict(p, precision=prec, **extra))
+        s.set_graph(graph)
+        s.init(**f)
+        for n in (1, 3, 400, 29, 300):  # starts on and off period boundaries (periods 14..140)
+            s.step(n)
+        runs.append((s.moments(), s.diag(), s.launches, s.t))
+    (mg, dg, lg, tg), (mp, dp, lp, tp) = runs
+    assert tg == tp == 733 and lg == lp
+    for k in mg:
+        assert np.array_equal(mg[k], mp[k]), k
+    assert np.array_equal(dg, dp)
