@@ -589,9 +589,11 @@ static int replay_period(lbm_ctx *c, int period) {
       if (e != cudaSuccess) rc = set_err(c, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
       if (!rc && c->p.diag_every > 0 && (t0 + k + 1) % c->p.diag_every == 0) {
         rc = enqueue_diag(c, c->diag_dev);
+        // an event record node the host can wait on (a plain record inside a
+        // capture only orders work within the graph)
         if (!rc && (cudaMemcpyAsync(c->h_diag, c->diag_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream) != cudaSuccess ||
-                    cudaEventRecord(c->diag_ev, c->stream) != cudaSuccess))
+                    cudaEventRecordWithFlags(c->diag_ev, c->stream, cudaEventRecordExternal) != cudaSuccess))
           rc = set_err(c, LBM_ECUDA, "graph capture of the diagnostics");
       }
     }
