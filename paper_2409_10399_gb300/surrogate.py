@@ -23,7 +23,8 @@ the LBM's increment for each channel, of the state, the persistence baseline
 lattices advanced window by window through lbm_surrogate_advance (surrogate,
 or the LBM from the lattice's own populations when the check fails), judged
 against the plain LBM's snapshots.  Speed: device time of one surrogate call
-against 64 LBM steps (FP32) of the same state.
+against 64 LBM steps (FP32) of the same state, as one 64-step call and as 1/100
+of a long graph-replayed run of the LBM.
 One JSON line per result.
 """
 import argparse
@@ -263,9 +264,19 @@ def speed(model, state, nx, ny, reps=20):
     e1.record()
     torch.cuda.synchronize()
     t_lbm = e0.elapsed_time(e1) / reps
+    # the same lattice run long: whole periods of steps replayed from a CUDA
+    # graph (lbm_step), the plain LBM at its fastest; per 64 steps
+    s.step(3200 - s.t % 3200)
+    torch.cuda.synchronize()
+    e0.record()
+    s.step(6400)
+    e1.record()
+    torch.cuda.synchronize()
+    t_long = e0.elapsed_time(e1) / 100
     s.close()
     flops = model_flops(model.nx, model.ny, model.channels, model.modes, model.layers)
     return dict(surrogate_ms=t_sur, lbm_64_steps_ms=t_lbm, speedup=t_lbm / t_sur,
+                lbm_64_steps_long_run_ms=t_long, speedup_vs_long_run=t_long / t_sur,
                 surrogate_tflops=flops / (t_sur * 1e-3) / 1e12, flops_per_call=flops)
 
 
