@@ -29,6 +29,9 @@ PARITY = {
     "collision+stream": "pinned: uniform fixed point, homogeneous ODE limit and steady state, "
                         "conservation, mirror symmetry, D2Q9/D3Q19 -> D1Q3 projection, brute force",
     "inlet/outlet": "pinned: TEST #1 outlet values (Sec. 3.6)",
+    "stabilisers": "pinned: Ohwada dashpot (sign, third liquid strategy) and the n_gamma latch phase against "
+                   "the homogeneous-state recurrence of Eqs. (lbm-cont-g1Dhat), (lbm-cont-l1Dhat), "
+                   "(lbm-cont-1D-update) (Sec. 3.2)",
     "fd": "partial: agreement with the LBM is qualitative in the paper (Sec. 3.6)",
 }
 
