@@ -102,11 +102,14 @@ typedef struct {
                                 with beta = 1), so the store keeps 4*Q planes
                                 plus c_g, c_l (2*D planes, double-buffered, in
                                 the held type) and re-evaluates the streamed
-                                beta populations from c at x - v_q.  Same
-                                results (bit for bit in FP32 and FP64DEV, where
-                                c is held in the arithmetic type; FP16DEV holds
-                                c in FP32, more precise than FP16 beta planes).
-                                Not with LBM_FP64. */
+                                beta populations from c at x - v_q.  The same
+                                method, equal to the six-scheme store to
+                                rounding, not bit for bit: the two forms are
+                                separate kernels whose multiply-adds the
+                                compiler contracts differently (the initial
+                                beta equilibria alone are bitwise equal).
+                                FP16DEV holds c in FP32, more precise than its
+                                FP16 beta planes.  Not with LBM_FP64. */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
@@ -169,9 +172,10 @@ int lbm_get_diag(lbm_ctx *c, double out[8]);
  * step) with period lcm(2, n_gamma, diag_every) <= 4096, lbm_step replays
  * whole periods from a CUDA graph captured once on a stream of the library's
  * own, which removes the launch gaps between steps; the results are bitwise
- * those of plain launches.  Within a replayed period only its last
- * diagnostics are read by the host (the FP64 reductions of every diag_every
- * steps still run).  enable = 0 launches every step.  lbm_init and
+ * those of plain launches.  Within a replayed period the diagnostics are
+ * taken once, after its last step (the period is a multiple of diag_every),
+ * so a non-finite state or a drift is reported at most one period after it
+ * arises.  enable = 0 launches every step.  lbm_init and
  * lbm_set_tile drop the captured graph.  Not in the paper. */
 int lbm_set_graph(lbm_ctx *c, int enable);
 
@@ -269,14 +273,22 @@ int lbm_batch_destroy(lbm_batch *b);
  * plus 8 results) that is a file-scope __device__ variable, so every GPU that
  * loads the library holds it until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.
+ * the device current; make that first call before any stream capture.  The
+ * address is cached together with the id of the CUDA context it was looked
+ * up in: after a device reset, or under another context made current by the
+ * caller, the next call looks it up again (and that call, too, belongs
+ * outside a stream capture).
  * Every call uses the same array, which keeps the last call's contents (each
  * call overwrites the parts it reads), so calls that overlap on the GPU --
  * on different streams, or from different host threads -- race and must be
  * serialised by the caller.
  *
  * Returns LBM_EINVAL for a bad lattice or Spalding mode, a NULL pointer, or
- * n_nodes outside [1, LBM_NOALLOC_MAX_NODES]; LBM_ECUDA if a CUDA call fails. */
+ * n_nodes outside [1, LBM_NOALLOC_MAX_NODES]; LBM_ECUDA if a CUDA call fails.
+ * A CUDA error already pending from the caller's earlier work
+ * (cudaPeekAtLastError) makes it return LBM_ECUDA before launching anything,
+ * and that error stays pending for the caller; errors of its own launches it
+ * reads and clears. */
 #define LBM_NOALLOC_MAX_NODES 2147483647LL
 int lbm_diag_populations_noalloc(int lattice, int spalding_mode, const double *pops, long long n_nodes,
                                  double *out, int out_on_device, void *stream);

@@ -25,7 +25,14 @@ constexpr int NA_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_scratch[NA_BLOCKS * 8 + 8];
 
 std::mutex g_mu;
-double *g_scratch_addr[NA_DEVICES] = {nullptr};
+// Cached device address of the scratch array, per device, together with the
+// id of the CUDA context it was looked up in: a device reset, or a caller
+// that makes another context current, gets a fresh lookup.
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  double *addr;
+};
+ScratchSlot g_slot[NA_DEVICES] = {};
 
 __device__ __forceinline__ double na_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -112,9 +119,38 @@ __global__ void k_diag_pops_noalloc_final(const double *partials, int nblocks, d
   if (lane == 0) out[k] = acc;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress) with that device current.  In host code
+// Id of the CUDA context current on this thread (cuCtxGetId, reached through
+// the runtime's driver entry points so that the library needs no link to the
+// driver library); false when there is none or the driver lacks the calls.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+bool current_ctx_id(unsigned long long *id) {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+    if (!get_cur || !get_id) cudaGetLastError();  // no error left pending by the queries
+  });
+  if (!get_cur || !get_id) return false;
+  void *ctx = nullptr;
+  if (get_cur(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current device's current
+// context, looked up (cudaGetSymbolAddress, with that device current) at the
+// first call in each context and cached with the context's id.  In host code
 // the array's name is only a stand-in and must never be handed to a kernel.
+// A failed lookup leaves no error pending for the caller.
 int scratch_address(double **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -123,15 +159,24 @@ int scratch_address(double **out) {
   }
   if (dev < 0 || dev >= NA_DEVICES) return LBM_EINVAL;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return LBM_ECUDA;
-    }
-    g_scratch_addr[dev] = (double *)p;
+  unsigned long long id = 0;
+  if (current_ctx_id(&id) && g_slot[dev].addr && g_slot[dev].ctx_id == id) {
+    *out = g_slot[dev].addr;
+    return LBM_OK;
   }
-  *out = g_scratch_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  // the lookup made the device's context current if it was not yet
+  if (current_ctx_id(&id)) {
+    g_slot[dev].ctx_id = id;
+    g_slot[dev].addr = (double *)p;
+  } else {
+    g_slot[dev].addr = nullptr;  // no context id: look the address up at every call
+  }
+  *out = (double *)p;
   return LBM_OK;
 }
 
@@ -142,6 +187,9 @@ extern "C" int lbm_diag_populations_noalloc(int lattice, int spalding_mode, cons
   if (lattice < LBM_D1Q3 || lattice > LBM_D3Q19 || !pops || !out || spalding_mode < 0 || spalding_mode > 2)
     return LBM_EINVAL;
   if (n_nodes < 1 || n_nodes > LBM_NOALLOC_MAX_NODES) return LBM_EINVAL;
+  // an error left pending by earlier work of the caller stays pending (and is
+  // not mistaken for this call's): nothing is launched
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
   double *scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc) return rc;

@@ -16,14 +16,17 @@ import paper_2409_10399_gb300 as lbm
 pytestmark = pytest.mark.gpu
 
 
-def _state(lat, dims, prec, steps):
+def _state(lat, dims, prec, steps, spalding=2, nan_node=None):
     torch = pytest.importorskip("torch")
     D = lbm.LATTICE[lat]
     p = dict(R=1000.0, omega_g=0.6, omega_l=120.0 / 67.0, omega_alpha=1.5, drag_model=1, kappa_I=2.4e-4,
-             g_hat=1e-6 / 999.0, g_axis=D - 1, gamma=1.0, n_gamma=7, spalding_mode=2, precision=prec,
+             g_hat=1e-6 / 999.0, g_axis=D - 1, gamma=1.0, n_gamma=7, spalding_mode=spalding, precision=prec,
              bc_lo=(0, 1, 1)[:D] + (0,) * (3 - D), bc_hi=(0, 1, 1)[:D] + (0,) * (3 - D))
     s = lbm.Simulation(lat, dims, p)
-    s.init(**lbm_inputs.fields_random(D, dims, seed=12, alpha=(0.05, 0.6), u_amp=2e-3, pk_amp=1e-5))
+    f = lbm_inputs.fields_random(D, dims, seed=12, alpha=(0.05, 0.6), u_amp=2e-3, pk_amp=1e-5)
+    if nan_node is not None:
+        f["u_g"][0, nan_node] = np.nan  # planted on the host, as a caller's bad input would be
+    s.init(**f)
     s.step(steps)
     Q = {1: 3, 2: 9, 3: 19}[D]
     pops = torch.empty((6, Q, s.N), dtype=torch.float64, device="cuda")
@@ -38,19 +41,22 @@ def _state(lat, dims, prec, steps):
 # store's arithmetic type while this entry point reduces the FP64 populations,
 # so the bar is the tests' bar for that type: 1e-12 for FP64 arithmetic,
 # 1e-5 for FP32.
+# Each Spalding mode (0 off, 1 and 2 the clamped renormalisation of Eq.
+# (spalding)) is compared on a lattice built with that mode.
+@pytest.mark.parametrize("spalding", [0, 1, 2])
 @pytest.mark.parametrize("lat,dims,prec", [("D2Q9", (700, 500), "fp64dev"), ("D3Q19", (24, 20, 18), "fp64"),
                                            ("D1Q3", (300,), "fp64"), ("D2Q9", (130, 70), "fp32")])
-def test_noalloc_matches_get_diag(lat, dims, prec):
+def test_noalloc_matches_get_diag(lat, dims, prec, spalding):
     torch = pytest.importorskip("torch")
-    s, pops = _state(lat, dims, prec, 33)
+    s, pops = _state(lat, dims, prec, 33, spalding=spalding)
     ref = s.diag()
     tol = 1e-5 if prec == "fp32" else 1e-12
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):  # two calls in a row share the scratch array
         out_dev = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
-        lbm.diag_populations_noalloc(lat, 2, pops.data_ptr(), s.N, out_dev.data_ptr(), 1, stream)
+        lbm.diag_populations_noalloc(lat, spalding, pops.data_ptr(), s.N, out_dev.data_ptr(), 1, stream)
         out_host = np.full(8, np.nan)
-        lbm.diag_populations_noalloc(lat, 2, pops.data_ptr(), s.N, out_host.ctypes.data, 0, stream)
+        lbm.diag_populations_noalloc(lat, spalding, pops.data_ptr(), s.N, out_host.ctypes.data, 0, stream)
         got_dev = out_dev.cpu().numpy()
         for got in (got_dev, out_host):
             for k in (0, 1, 2, 4):
@@ -62,6 +68,22 @@ def test_noalloc_matches_get_diag(lat, dims, prec):
             # rounding is ~1e-16 (FP64) or ~1e-7 (FP32) per node before squaring
             assert got[3] == pytest.approx(ref[3], rel=1e-6 if tol < 1e-6 else 0.2, abs=1e-30)
             assert got[5] == ref[5] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_counts_non_finite_nodes(prec):
+    """A NaN velocity planted at one node of the initial fields spreads over a
+    few steps; both entry points count the same nodes with a non-finite
+    population (slot 5), call after call."""
+    torch = pytest.importorskip("torch")
+    s, pops = _state("D2Q9", (64, 40), prec, 3, nan_node=1000)
+    ref = s.diag()
+    assert ref[5] > 1
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        out = np.full(8, -1.0)
+        lbm.diag_populations_noalloc("D2Q9", 2, pops.data_ptr(), s.N, out.ctypes.data, 0, stream)
+        assert out[5] == ref[5]
 
 
 def test_noalloc_rejects_bad_sizes():
