@@ -157,7 +157,7 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
     a.bc_hi[d] = d < c->D ? p.bc_hi[d] : BC_PERIODIC;
   }
   a.parity = (int)(t & 1);
-  a.latch = (t % p.n_gamma) == 0;
+  a.latch = (t % p.n_gamma) == 0 || c->first_step;
   a.g_axis = p.g_axis;
   a.tr_axis = -1;
   for (int d = 0; d < c->D; d++)
@@ -207,7 +207,7 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.ulIN = p.inlet_ul_mode == 1 ? -a.aIN * a.ugIN / (1.0 - a.aIN) : ramp(p.in_ul, t, p.ramp_nt);
   a.plain = c->prec == LBM_FP64;
   a.cfield = c->cfield;
-  a.beta_own = c->cfield && t == 0;
+  a.beta_own = c->cfield && c->first_step;
   a.off32 = (long long)c->Q * c->plane < (1LL << 32);
   // the same constants in the kernels' arithmetic types
   PhysT<double> &d = a.pd;
@@ -348,6 +348,7 @@ static int init_fields(lbm_ctx *c, const double *da, const double *dug, const do
   MomArgs ma = make_mom(c, nullptr);
   CUDA_TRY(c, dispatch_init(c, ma, da, dug, dul, dpk));
   c->mass0 = alpha_sum;
+  c->first_step = 1;
   c->initialised = 1;
   c->sticky = 0;
   c->diag_pending = 0;
@@ -538,6 +539,7 @@ static int enqueue_diag(lbm_ctx *c, double *dev_out) {
 static int one_step(lbm_ctx *c) {
   StepArgs a = make_args(c, c->t);
   CUDA_TRY(c, dispatch_step(c, a));
+  c->first_step = 0;
   c->t++;
   if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
     if (c->diag_pending) {
@@ -557,11 +559,11 @@ static long long gcd_ll(long long a, long long b) { return b ? gcd_ll(b, a % b) 
 
 // Period after which the step arguments (parity, lag latch, diagnostics)
 // repeat exactly, or 0 when they do not (an inlet ramp still changing them,
-// the beta-stencil form's first step) or the period would be long.
+// the first step after an initialisation) or the period would be long.
 static int graph_period(const lbm_ctx *c) {
   if (!c->use_graph) return 0;
   if (c->p.bc_lo[c->p.g_axis] == LBM_BC_INLET && c->p.ramp_nt > 0) return 0;
-  if (c->cfield && c->t == 0) return 0;
+  if (c->first_step) return 0;
   long long per = c->p.n_gamma % 2 == 0 ? c->p.n_gamma : 2LL * c->p.n_gamma;
   if (c->p.diag_every > 0) per = per / gcd_ll(per, c->p.diag_every) * c->p.diag_every;
   return per <= 4096 ? (int)per : 0;
@@ -569,7 +571,10 @@ static int graph_period(const lbm_ctx *c) {
 
 // One period from the graph, captured at its first use on a stream of the
 // lattice's own (the legacy default stream cannot be captured) and replayed on
-// the lattice's stream.  Only the last diagnostics of a period reach the host.
+// the lattice's stream.  The diagnostics are taken once per period, after its
+// last step (the period is a multiple of diag_every): one reduction, one copy
+// to the host and one event record per replay, so the host's wait on the
+// event is a wait on that copy.
 static int replay_period(lbm_ctx *c, int period) {
   if (c->diag_pending) {
     int rc = check_diag(c, 1);
@@ -587,7 +592,7 @@ static int replay_period(lbm_ctx *c, int period) {
       StepArgs a = make_args(c, t0 + k);
       cudaError_t e = dispatch_step(c, a);
       if (e != cudaSuccess) rc = set_err(c, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-      if (!rc && c->p.diag_every > 0 && (t0 + k + 1) % c->p.diag_every == 0) {
+      if (!rc && c->p.diag_every > 0 && k == period - 1) {
         rc = enqueue_diag(c, c->diag_dev);
         // an event record node the host can wait on (a plain record inside a
         // capture only orders work within the graph)

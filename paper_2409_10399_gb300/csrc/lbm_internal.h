@@ -22,6 +22,11 @@ struct lbm_ctx {
   size_t stage_bytes = 0;
   cudaStream_t stream = 0;
   long long t = 0;
+  // the next step is the first since an initialisation (lbm_init, or the
+  // surrogate window's re-initialisation at a later clock): it latches S''
+  // and Lambda' and, in the beta-stencil form, takes every q from the node's
+  // own c, whatever t is
+  int first_step = 0;
   int initialised = 0, sticky = 0;
   double r_ag = 0.5, r_al = 0.5;
   double mass0 = 0.0;

@@ -171,11 +171,11 @@ def test_adam_step_is_the_textbook_update():
     assert np.abs(m.grads()).max() == 0.0  # zeroed after the step
 
 
-def _lattice(dims=DIMS, seed=5, prec="fp64"):
+def _lattice(dims=DIMS, seed=5, prec="fp64", **extra):
     import lbm_inputs
     from paper_2409_10399_gb300 import surrogate as S
     nx, ny = dims[0], dims[1]
-    sim = lbm.Simulation("D2Q9", (nx, ny), S._lbm_params(prec))
+    sim = lbm.Simulation("D2Q9", (nx, ny), dict(S._lbm_params(prec), **extra))
     sim.init(**lbm_inputs.fields_plumes(nx, ny, seed))
     return sim
 
@@ -222,6 +222,41 @@ def test_surrogate_window_on_an_fp32_lattice():
     assert _rel(a[1:5], b[1:5]) < 1e-5
     sim.step(64)  # the lattice carries on from the re-initialised state
     assert np.isfinite(_state_of(sim)).all() and sim.t == 128
+
+
+@pytest.mark.parametrize("prec,bstencil", [("fp64", 0), ("fp64dev", 0), ("fp64dev", 1)])
+def test_surrogate_reinit_steps_like_a_fresh_init(prec, bstencil):
+    """After an accepted window the lattice is re-initialised at clock
+    t + window (64 here, not a multiple of n_gamma = 200).  Its next steps must
+    be those of a twin given the same fields by lbm_init at t = 0: the first
+    step after either initialisation latches S'' and Lambda' (Eq.
+    (lbm-cont-1D-update)) and, in the beta-stencil form, evaluates the
+    streamed beta populations from each node's own c (the initial state holds
+    f^eq(1, c(x)) at x).  Twenty steps stay before the next latch of either
+    clock.  FP64: bitwise.  FP64-deviation forms: the deviation reference is
+    the predicted mean alpha_g, summed on the device by the window and on the
+    host by lbm_init, so the two agree to double rounding (1e-12)."""
+    p, _, _, norm = _case(seed=18)
+    m = _model(p, norm)
+    sim = _lattice(prec=prec, beta_stencil=bstencil)
+    now = _state_of(sim)
+    _, used = m.advance_lattice(sim, 64, max_drift=1e30)
+    assert used and sim.t == 64
+    pred = torch.empty((6, now.shape[1]), dtype=torch.float64, device="cuda")
+    m.advance(torch.from_numpy(now).cuda().contiguous(), pred, max_drift=1e30)
+    pred = pred.cpu().numpy()
+    twin = _lattice(prec=prec, beta_stencil=bstencil)
+    twin.init(alpha_g=pred[0], u_g=pred[1:3], u_l=pred[3:5], p_k=pred[5])
+    sim.step(20)
+    twin.step(20)
+    assert sim.t == 84 and twin.t == 20
+    a, b = sim.moments(), twin.moments()
+    for k in ("alpha_g", "u_g", "u_l", "p_k", "S_g", "S_l"):
+        if prec == "fp64":
+            assert np.array_equal(a[k], b[k]), k
+        else:
+            ref = b[k] - (1 / 3 if k == "p_k" else 0.0)
+            assert np.linalg.norm(a[k] - b[k]) <= 1e-12 * np.linalg.norm(ref), k
 
 
 def test_surrogate_window_falls_back_to_the_lattice_steps():
