@@ -7,7 +7,8 @@ so the bar is the FP32 parity bar applied node by node (max difference <= 1e-5
 of the field's scale after 31 steps; one-step differences are ~5e-8), with and without CUDA-graph
 replay and for step counts that are not multiples of the graph period.  Within
 the batched kernel the result is bitwise independent of the tile and of graph
-replay.  One instance is also checked against the oracle."""
+replay.  Every instance of a ragged batch spanning R = 10..1000 is also
+checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -72,21 +73,21 @@ def test_batch_tile_independent_and_graph_replays():
                     assert np.array_equal(a[k], r[k])
 
 
-def test_batch_instance_against_oracle():
-    dims, p, f = _cases()[1]
-    b = lbm.Batch("D2Q9", [dims], [p])
-    b.init(0, **f)
+def test_batch_instances_against_oracle():
+    """Every instance of one ragged batch (sizes 9 x 11 to 128 x 20, R from 10
+    to 1000, drag coefficients 1e-4 to 5e-3) against its own FP64 oracle run,
+    per field at the FP32 bar (u_l on the scale of test_gpu_parity.u_l_scale)."""
+    from test_gpu_parity import assert_parity
+    cases = _cases()
+    b = lbm.Batch("D2Q9", [d for d, _, _ in cases], [p for _, p, _ in cases])
+    for i, (_, _, f) in enumerate(cases):
+        b.init(i, **f)
     b.step(120)
-    got = b.moments(0)
-    o = oracle.Oracle("D2Q9", dims + (1,), p, threads=8)
-    o.init(**f)
-    o.step(120)
-    ref = o.moments()
-    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)
-    assert rel(got["alpha_g"], ref["alpha_g"]) < 1e-5
-    u = np.concatenate([got["u_g"].ravel(), got["u_l"].ravel()])
-    ur = np.concatenate([ref["u_g"].ravel(), ref["u_l"].ravel()])
-    assert rel(u, ur) < 1e-5
+    for i, (dims, p, f) in enumerate(cases):
+        o = oracle.Oracle("D2Q9", dims + (1,), p, threads=8)
+        o.init(**f)
+        o.step(120)
+        assert_parity(b.moments(i), o.moments(), "fp32", "batch instance %d" % i, R=p["R"])
 
 
 def test_batch_rejects_inconsistent_instances():

@@ -78,7 +78,7 @@ def test_stencil_form_fp16_against_oracle(name):
     lat, dims, p, steps = CASES[name]
     f = case_fields(lat, dims, seed=zlib.crc32(name.encode()) % 997)
     got, ref, _, _ = run_pair(lat, dims, dict(p, beta_stencil=1), f, min(steps, 200), "fp16dev")
-    assert_parity(got, ref, "fp16dev", name + " stencil")
+    assert_parity(got, ref, "fp16dev", name + " stencil", R=p["R"])
 
 
 @pytest.mark.parametrize("name", ["d2q9_walls", "d3q19_strip"])
@@ -86,7 +86,7 @@ def test_stencil_form_fp32_against_oracle(name):
     lat, dims, p, steps = CASES[name]
     f = case_fields(lat, dims, seed=zlib.crc32(name.encode()) % 997)
     got, ref, _, _ = run_pair(lat, dims, dict(p, beta_stencil=1), f, min(steps, 200), "fp32")
-    assert_parity(got, ref, "fp32", name + " stencil")
+    assert_parity(got, ref, "fp32", name + " stencil", R=p["R"])
 
 
 def test_stencil_form_rejected_where_undefined():

@@ -70,3 +70,38 @@ def test_no_false_alarm_on_a_healthy_run():
         s.step(10)
     d = s.diag()
     assert d[5] == 0 and np.isfinite(d[:5]).all()
+
+
+def test_non_finite_state_found_within_replayed_periods():
+    """A state that turns non-finite only after many steps (a BGK lattice at
+    omega = 1.99 started from velocities of 0.3, far above what the scheme
+    can carry, which blows up), stepped a whole graph period per call
+    (n_gamma = 7, diag_every = 7: period 14).  With graph replay the
+    diagnostics are taken once per period, after its last step; both paths
+    report LBM_ENAN, the replayed one at most one call after the one that
+    launches every step, and the error is sticky."""
+    import torch
+    f = _fields(seed=6)
+    r = np.random.default_rng(6)
+    f["u_g"] = r.uniform(-0.3, 0.3, f["u_g"].shape)
+    f["u_l"] = r.uniform(-0.3, 0.3, f["u_l"].shape)
+    found = {}
+    for graph in (False, True):
+        s = lbm.Simulation("D2Q9", DIMS, dict(BASE, omega_g=1.99, omega_l=1.99, diag_every=7))
+        s.set_graph(graph)
+        s.init(**f)
+        for call in range(300):
+            try:
+                s.step(14)
+            except lbm.LBMError as e:
+                assert e.code == -4, e
+                found[graph] = call
+                break
+            torch.cuda.synchronize()
+        else:
+            pytest.fail("no LBM_ENAN in 300 periods (graph=%s)" % graph)
+        with pytest.raises(lbm.LBMError) as e:
+            s.step(14)
+        assert e.value.code == -7
+    assert found[False] >= 1  # the state was finite for the first period
+    assert 0 <= found[True] - found[False] <= 1, found

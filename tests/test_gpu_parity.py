@@ -48,18 +48,28 @@ def run_pair(lat, dims, p, fields, steps, prec, threads=8):
     return got, ref, s, o
 
 
-def assert_parity(got, ref, prec, ctx=""):
-    """alpha_g and p_k: relative L2 per field.  u: relative L2 of the two-phase
-    velocity field (u_g, u_l) taken together -- at R = 1000 the liquid of a
-    closed column is nearly at rest, and a per-phase ratio would measure
-    rounding against a field that is almost zero."""
+def u_l_scale(ref, R):
+    """Denominator of the liquid velocity's relative error: max(|u_l|, |u_g|/R)
+    over the reference field.  The liquid's momentum receives the interphase
+    force divided by R (Eq. (Gl), drag term of Eq. (interphasemomentum)), so a
+    liquid brought nearly to rest (RMS 1e-9 in the test states, where the gas
+    moves at 1e-4) carries, relative to the gas, the gas velocity's error
+    scaled by 1/R; below |u_g|/R the liquid's own norm would measure rounding
+    against a field the coupling does not resolve.  Wherever |u_l| >= |u_g|/R
+    this is the plain per-phase relative error."""
+    return max(np.linalg.norm(ref["u_l"]), np.linalg.norm(ref["u_g"]) / R)
+
+
+def assert_parity(got, ref, prec, ctx="", R=1000.0):
+    """Relative L2 per field: alpha_g, u_g, u_l (denominator u_l_scale) and
+    p_k; S_g, S_l on the scale of max |S|."""
     tol = TOL[prec]
-    for k in ("alpha_g", "p_k"):
+    for k in ("alpha_g", "p_k", "u_g"):
         e = rel(got[k], ref[k])
         assert e <= tol, "%s %s rel L2 %.3e > %.1e" % (ctx, k, e, tol)
-    e = rel(np.concatenate([got["u_g"].ravel(), got["u_l"].ravel()]),
-            np.concatenate([ref["u_g"].ravel(), ref["u_l"].ravel()]))
-    assert e <= tol, "%s u rel L2 %.3e > %.1e" % (ctx, e, tol)
+    e = np.linalg.norm(np.asarray(got["u_l"]) - ref["u_l"]) / u_l_scale(ref, R)
+    assert e <= tol, "%s u_l rel L2 %.3e > %.1e (|u_l| %.2e, |u_g|/R %.2e)" % (
+        ctx, e, tol, np.linalg.norm(ref["u_l"]), np.linalg.norm(ref["u_g"]) / R)
     # S = 1 - beta is a small difference: compare on the scale of max |S|
     for k in ("S_g", "S_l"):
         e = np.abs(got[k] - ref[k]).max()
@@ -122,7 +132,7 @@ def test_parity_cases(name, prec):
         steps = min(steps, FP32_STEPS)
     f = case_fields(lat, dims, seed=zlib.crc32(name.encode()) % 997)
     got, ref, _, _ = run_pair(lat, dims, p, f, steps, prec)
-    assert_parity(got, ref, prec, name)
+    assert_parity(got, ref, prec, name, R=p["R"])
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -147,7 +157,7 @@ def test_parity_fp64dev(name):
     lat, dims, p, steps = CASES[name]
     f = case_fields(lat, dims, seed=zlib.crc32(name.encode()) % 997)
     got, ref, _, _ = run_pair(lat, dims, p, f, steps, "fp64dev")
-    assert_parity(got, ref, "fp64dev", name)
+    assert_parity(got, ref, "fp64dev", name, R=p["R"])
 
 
 @pytest.mark.parametrize("name", ["d2q9_walls", "d3q19_walls", "d2q9_strip"])
@@ -160,7 +170,7 @@ def test_parity_fp16dev(name):
     f = lbm_inputs.fields_column3d(d3[0], d3[1], d3[2], seed=5, corr=2.0)
     f = dict(alpha_g=f["alpha_g"], p_k=f["p_k"], u_g=f["u_g"][:D], u_l=f["u_l"][:D])
     got, ref, _, _ = run_pair(lat, dims, p, f, min(steps, 100), "fp16dev")
-    assert_parity(got, ref, "fp16dev", name)
+    assert_parity(got, ref, "fp16dev", name, R=p["R"])
 
 
 @pytest.mark.parametrize("steps", [0, 1, 2, 3])
@@ -302,12 +312,16 @@ def test_results_independent_of_tile(prec):
     ("d3q19_walls", "fp32", dict(diag_every=6)),
     ("d1q3_walls", "fp64", dict(diag_every=35)),
     ("d2q9_walls", "fp32", dict(beta_stencil=1, diag_every=0)),
+    ("d2q9_walls", "fp32", dict(diag_every=1)),
 ])
 def test_graph_replay_is_bitwise_plain_launches(name, prec, extra):
     """lbm_step replays periods of lcm(2, n_gamma, diag_every) steps from a CUDA
     graph when the step arguments repeat (closed lattices): the fields are
     bitwise those of plain launches, over whole periods and ragged remainders,
-    the diagnostics agree, and the launch count is the same."""
+    and the diagnostics agree.  A replayed period takes its diagnostics once,
+    after its last step (diag_every = 1 gives 14 reductions per period
+    launched one by one, one replayed), so the graph path launches fewer
+    kernels when diagnostics are on and the same number when they are off."""
     lat, dims, p, _ = CASES[name]
     f = case_fields(lat, dims, seed=9)
     runs = []
@@ -319,7 +333,8 @@ def test_graph_replay_is_bitwise_plain_launches(name, prec, extra):
             s.step(n)
         runs.append((s.moments(), s.diag(), s.launches, s.t))
     (mg, dg, lg, tg), (mp, dp, lp, tp) = runs
-    assert tg == tp == 733 and lg == lp
+    assert tg == tp == 733
+    assert lg == lp if extra.get("diag_every", 0) == 0 else lg < lp
     for k in mg:
         assert np.array_equal(mg[k], mp[k]), k
     assert np.array_equal(dg, dp)
