@@ -3,16 +3,25 @@
 
 One "step" is one time step of the whole hot path (moments, sources,
 coupling, stabilisers, drag, forces, six collisions, AA streaming with the
-face rules, plus the FP64 diagnostics every DIAG_EVERY steps) over the 2D
-bubble-column box: D2Q9, 512 x 2048 nodes, FP32 store and arithmetic,
-R = 1000, CGW drag, bottom inlet strip.  The store (466 MB) is larger than
-L2, so no flush is needed between steps.
+face rules) over the 2D bubble-column box: D2Q9, 512 x 2048 nodes, FP32 store
+and arithmetic, R = 1000, CGW drag, bottom inlet strip.  The library also
+enqueues its FP64 diagnostics after every DIAG_EVERY-th step; a timed run of K
+steps contains floor((t0 + K)/DIAG_EVERY) - floor(t0/DIAG_EVERY) of them (none
+for the default 20 steps after 5 warm-up steps), reported as
+`diag_passes_timed`.  The store (466 MB) is larger than L2, so no flush is
+needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--no-cpu-baseline] [--no-forms] [--quick-forms]
 
-Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
-replica (different seed), timing is the max over ranks and `value` the
-aggregate; there is no data-path collective.
+Prints one JSON line.  Besides the benchmark's own keys it carries `forms`:
+every other form of the method timed live on the same GPU at its workload's
+full size (FP16-deviation store, FP64 reference path, the batched sweep, the
+learned surrogate, the 1D column), each with its speedup over the plain FP32
+and FP64 single-lattice paths and the accuracy it is run at
+(paper_2409_10399_gb300/forms.py).  Under torchrun (N > 1) every rank
+advances its own replica (different seed), timing is the max over ranks and
+`value` the aggregate; there is no data-path collective.
 """
 import argparse
 import hashlib
@@ -38,7 +47,10 @@ STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 2}
 HELD_BYTES = {"fp64": 8, "fp32": 4, "fp16dev": 4}
 Q_OF = {"D1Q3": 3, "D2Q9": 9, "D3Q19": 19}
 KERNEL_SRC = os.path.join(ROOT, "paper_2409_10399_gb300", "csrc", "lbm_kernels.cuh")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_step_box2d_fp32.md")
+# DRAM bytes (read + write) per launch of the box2d FP32 step kernel from one
+# ncu capture, valid only for the kernel source it was taken on (the SHA-256
+# prefix of lbm_kernels.cuh); otherwise the bench reports traffic null.
+NCU_TRAFFIC = {"kernel_source_sha16": "ce7f4e45342a6845", "bytes_per_launch": 407311616.0}
 
 
 def bytes_per_node(lattice, prec):
@@ -68,24 +80,28 @@ def kernel_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def ncu_traffic():
+    """DRAM traffic per launch from the ncu capture of the current kernel
+    source, else None."""
+    return NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_source_sha16"] == kernel_hash() else None
+
+
+def cpu_model():
     try:
-        txt = open(PROFILE_SUMMARY).read()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
     except OSError:
-        return None
-    kv = {}
-    for line in txt.splitlines():
-        if "=" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split("=", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_sha256") != kernel_hash():
-        return None
-    try:
-        return float(kv["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+        pass
+    import platform
+    return platform.machine()
 
 
 class ClockSampler:
@@ -163,17 +179,16 @@ def replica_seed(base, rank):
     return base + rank
 
 
-def cpu_baseline(budget_s=15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: a
-    512 x 64 strip of the box (same physics, inlet strip, walls), all host
-    cores, for as many steps as fit in about `budget_s` seconds."""
+def _oracle_rate(threads, budget_s):
+    """Node updates per second of the FP64 oracle, as it stands, on a 512 x 64
+    strip of the box (same physics, inlet strip, walls) with `threads`
+    OpenMP threads, for as many steps as fit in about `budget_s` seconds."""
     import oracle
     from oracle import params as oparams
     w = lbm_inputs.WORKLOADS[WORKLOAD]
     nx, ny = w["dims"][0], 64
     f = lbm_inputs.fields_box2d(nx, ny, seed=2)
-    cores = os.cpu_count() or 1
-    o = oracle.Oracle(w["lattice"], (nx, ny, 1), oparams.lattice_params(w["physics"]), threads=cores)
+    o = oracle.Oracle(w["lattice"], (nx, ny, 1), oparams.lattice_params(w["physics"]), threads=threads)
     o.init(**f)
     o.step(2)
     t0 = time.perf_counter()
@@ -183,9 +198,19 @@ def cpu_baseline(budget_s=15.0):
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": "%dx%d strip of the box (inlet strip, walls, same physics), %d steps, FP64 C, OpenMP"
-                      % (nx, ny, steps)}
+    return nx * ny * steps / dt, nx, ny, steps
+
+
+def cpu_baseline(budget_s=10.0):
+    """The FP64 oracle on the host cores: all of them (the baseline value) and
+    one thread, on the same bounded sample of the workload."""
+    cores = os.cpu_count() or 1
+    rate, nx, ny, steps = _oracle_rate(cores, budget_s)
+    rate1, _, _, steps1 = _oracle_rate(1, budget_s)
+    return {"value": rate / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%dx%d strip of the box (inlet strip, walls, same physics), %d steps at %d threads and %d "
+                      "at 1, FP64 C, OpenMP" % (nx, ny, steps, cores, steps1),
+            "single_thread_value": rate1 / 1e6, "cpu_model": cpu_model()}
 
 
 def run_reference(args, rank, world):
@@ -252,10 +277,18 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     K = args.steps
-    # per-kernel timing: an event pair around every SAMPLE-th step kernel
-    SAMPLE = 16
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (K // SAMPLE + 1))]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # The timed region: exactly K steps on the library's stream between two
+    # events.  The run is cut into segments at the steps after which the
+    # library enqueues its diagnostics, with an event at every cut; the step
+    # kernel's average launch duration is the time of the segments that hold
+    # step kernels only, over their launches.  Before the start event a torch
+    # sleep kernel keeps the GPU busy while the launches are queued, so no
+    # host gap between launches is timed.
+    t0_steps = sim.t
+    cuts = sorted(set([0, K] + [k for k in range(K) if (t0_steps + k + 1) % DIAG_EVERY == 0] +
+                      [k + 1 for k in range(K) if (t0_steps + k + 1) % DIAG_EVERY == 0]))
+    cuts = [k for k in cuts if 0 <= k <= K]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in cuts]
     clocks = ClockSampler(torch.cuda.current_device())
     if dist:
         dist.barrier()
@@ -264,29 +297,27 @@ def run_native(args, rank, world, local_rank):
     time.sleep(0.3)
     l0 = sim.launches
     t0_wall = time.perf_counter()
-    t_start.record(stream)
-    k = 0
-    while k < K:
-        j = k // SAMPLE
-        ev[2 * j].record(stream)
-        sim.step(1)
-        ev[2 * j + 1].record(stream)
-        n = min(SAMPLE - 1, K - k - 1)
-        if n:
-            sim.step(n)
-        k += 1 + n
-    t_end.record(stream)
+    torch.cuda._sleep(2_000_000)
+    ev[0].record(stream)
+    for j in range(1, len(cuts)):
+        sim.step(cuts[j] - cuts[j - 1])
+        ev[j].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0_wall
     if dist:
         dist.barrier()
     clk = clocks.stop()
     launches = sim.launches - l0
-    t_total = t_start.elapsed_time(t_end) / 1e3
-    t0 = sim.t - K
-    step_times = [ev[2 * j].elapsed_time(ev[2 * j + 1]) / 1e3 for j in range((K + SAMPLE - 1) // SAMPLE)
-                  if (t0 + j * SAMPLE + 1) % DIAG_EVERY != 0]
-    kern_s = sum(step_times) / len(step_times)
+    t_total = ev[0].elapsed_time(ev[-1]) / 1e3
+    pure_t, pure_n, diag_passes = 0.0, 0, 0
+    for j in range(1, len(cuts)):
+        n = cuts[j] - cuts[j - 1]
+        has_diag = (t0_steps + cuts[j]) % DIAG_EVERY == 0
+        diag_passes += int(has_diag)
+        if not has_diag:
+            pure_t += ev[j - 1].elapsed_time(ev[j]) / 1e3
+            pure_n += n
+    kern_s = pure_t / pure_n if pure_n else t_total / K
     t_total = reduce_max(t_total, dist, "cuda")
     diag = sim.diag()
     if diag[5] != 0:
@@ -327,16 +358,21 @@ def run_native(args, rank, world, local_rank):
                    "diag_every": DIAG_EVERY, "l2": "store %.0f MB > 129 MB L2, no flush" % (N * (6 * Q_OF[lat] * STORE_BYTES[prec] + 3 * HELD_BYTES[prec]) / 1e6),
                    "parallelism": "replicas x%d" % world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(), "kernel": "k_step<D2Q9,float,float>",
+                     "traffic": ncu_traffic(), "kernel": "k_step<D2Q9,float,float>",
                      "bytes_per_node": bpn, "kernel_ms": kern_s * 1e3, "peak_source": peak_kind},
         "e2e": {"value": aggregate_mlups(N, K, world, t_e2e), "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
         "gpu_launches": launches,
+        "diag_passes_timed": diag_passes,
         "clocks": clk,
         "wall_s": wall,
     }
+    sim.close()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_forms:
+        from paper_2409_10399_gb300 import forms
+        line["forms"] = forms.all_forms(stream, quick=args.quick_forms)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -349,6 +385,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other forms (FP16, FP64, batch, surrogate)")
+    ap.add_argument("--quick-forms", action="store_true", help="the forms' accuracy runs at a tenth of their steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
