@@ -50,8 +50,14 @@ enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2, LBM_D3Q19 = 3 };
  *   for the alpha schemes) and float arithmetic written in those deviations.
  * FP16DEV: half store of the same deviations, float arithmetic.
  * FP64DEV: the FP32 kernel's deviation arithmetic in double (validation of
- *   the fast path's algebra at double precision). */
-enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_FP64DEV = 3 };
+ *   the fast path's algebra at double precision).
+ * FP16AB: f_g and f_l (the phase momenta and pressure, Sec. 2.1.1) in the
+ *   float store, f_alpha and f_beta (Secs. 2.2, 2.3) in the half store;
+ *   float arithmetic.  The liquid velocity is the first moment of f_l, which
+ *   in half storage keeps 11 significant bits per population per step; this
+ *   form carries it at FP32 resolution for 16 instead of 24 bytes per
+ *   direction and node. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_FP64DEV = 3, LBM_FP16AB = 4 };
 
 /* Face conditions.  WALL: half-way bounce-back for all six schemes (Eq.
  * (BCINLET), BB rule with zero wall velocity).  INLET: Table 1, only on the
@@ -91,7 +97,7 @@ typedef struct {
   int ramp_nt;               /* n_t of Eq. (transient); <= 0: the max at once */
   int inlet_ul_mode;         /* 0: u_l^IN ramp; 1: u_l^IN = -a u_g^IN/(1-a)
                                 (zero net volume flux through the strip) */
-  int precision;             /* LBM_FP64 / LBM_FP32 / LBM_FP16DEV / LBM_FP64DEV */
+  int precision;             /* LBM_FP64 / LBM_FP32 / LBM_FP16DEV / LBM_FP64DEV / LBM_FP16AB */
   int diag_every;            /* > 0: FP64 diagnostics every that many steps
                                 inside lbm_step, checked for NaN / drift */
   double drift_limit;        /* relative drift of sum(a_g) that raises

@@ -18,7 +18,7 @@ __all__ = ["Simulation", "Batch", "Surrogate", "LBMError", "load_library", "latt
            "PRECISION", "LATTICE", "BC"]
 
 LATTICE = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
-PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "fp64dev": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "fp64dev": 3, "fp16ab": 4}
 BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
 ERRORS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ENAN",
           -5: "LBM_EDRIFT", -6: "LBM_ETIMEOUT", -7: "LBM_ESTATE"}

@@ -1,7 +1,8 @@
 """Error and throughput of the precision forms on the workloads.
 
     python -m paper_2409_10399_gb300.accuracy [--study box2d|column3d|column1d|all|
-                                                sensitivity|spalding|bstencil|column3d_small]
+                                                sensitivity|spalding|bstencil|column3d_small|
+                                                fp64_launches]
 
 For each study the same seeded state is advanced with the FP64 reference path
 (bitwise equal to the CPU oracle on every case the tests cover) and with the
@@ -101,14 +102,15 @@ def sensitivity(name, rel_perturbation, steps=None, dims=None, seed=99):
                 err_pk=_rel(b["p_k"] - 1 / 3, a["p_k"] - 1 / 3))
 
 
-def throughput(name, form, steps=200, dims=None, beta_stencil=0):
+def throughput(name, form, steps=200, dims=None, beta_stencil=0, warm=20):
     """Device time per step of one form at the workload's full size."""
     w = lbm_inputs.WORKLOADS[name]
     dims = dims or w["dims"]
     f = lbm_inputs.fields_for(name, dims=dims)
     N = int(np.prod(dims))
     p = dict(lparams.lattice_params(w["physics"], precision=form), beta_stencil=beta_stencil)
-    _run(w["lattice"], dims, p, f, 20)
+    if warm:
+        _run(w["lattice"], dims, p, f, warm)
     m, ms, d = _run(w["lattice"], dims, p, f, steps)
     return dict(study=name + "_throughput", dims=list(dims), steps=steps, form=form, beta_stencil=beta_stencil,
                 us_per_step=ms * 1e3, MLUPS=N / ms / 1e3, nonfinite=int(d[5]))
@@ -120,6 +122,12 @@ def main():
     ap.add_argument("--spalding", type=int, default=None, help="override the Spalding mode of the workloads")
     args = ap.parse_args()
     todo = []
+    if args.study == "fp64_launches":
+        # two launches of the FP64 reference step on each workload recipe at
+        # a size one capture can hold (the FP64 operation counts of the
+        # reference kernels are taken with ncu on these launches)
+        todo.append(lambda: [throughput(n, "fp64", steps=2, dims=d, warm=0) for n, d in
+                             (("column1d", (512, 1, 1)), ("box2d", (512, 256, 1)), ("column3d", (64, 64, 128)))])
     if args.study == "column3d_small":
         # D3Q19 at 128 x 128 x 256 (2 GB of store traffic per step): the
         # profiling case of the 3D kernels

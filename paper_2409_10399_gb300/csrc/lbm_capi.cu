@@ -89,8 +89,11 @@ static int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return set_err((c), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-static size_t store_size(int prec) {
-  return (prec == LBM_FP64 || prec == LBM_FP64DEV) ? 8 : (prec == LBM_FP32 ? 4 : 2);
+// Bytes of one direction of one node of the whole population store (nsch
+// schemes): FP16AB keeps f_g, f_l in float and the other schemes in half.
+static size_t store_bytes_per_dir(int prec, int nsch) {
+  if (prec == LBM_FP16AB) return 2 * 4 + (size_t)(nsch - 2) * 2;
+  return (size_t)nsch * ((prec == LBM_FP64 || prec == LBM_FP64DEV) ? 8 : (prec == LBM_FP32 ? 4 : 2));
 }
 static size_t held_size(int prec) { return (prec == LBM_FP64 || prec == LBM_FP64DEV) ? 8 : 4; }
 
@@ -208,6 +211,7 @@ static StepArgs make_args(const lbm_ctx *c, long long t) {
   a.plain = c->prec == LBM_FP64;
   a.cfield = c->cfield;
   a.beta_own = c->cfield && c->first_step;
+  a.halo_off = c->halo_off;
   a.off32 = (long long)c->Q * c->plane < (1LL << 32);
   // the same constants in the kernels' arithmetic types
   PhysT<double> &d = a.pd;
@@ -270,6 +274,7 @@ template <int LAT> static int bound_threads(int prec) {
   if (prec == LBM_FP32) return StepBounds<Lattice<LAT>, float>::threads;
   if (prec == LBM_FP16DEV) return StepBounds<Lattice<LAT>, __half>::threads;
   if (prec == LBM_FP64DEV) return StepBounds<Lattice<LAT>, double>::threads;
+  if (prec == LBM_FP16AB) return StepBounds<Lattice<LAT>, MixAB>::threads;
   return 256;
 }
 
@@ -317,6 +322,15 @@ static int choose_tiles(lbm_ctx *c) {
   } else {
     c->smem = 0;
   }
+  // beta-stencil form: the block's c tile plus a one-node halo, 2*D values
+  // per node in the held type, after the exchange area (16-byte aligned)
+  c->halo_off = 0;
+  if (c->cfield || c->p.beta_stencil) {
+    const size_t box = (size_t)(c->T[0] + 2) * (c->D > 1 ? c->T[1] + 2 : 1) * (c->D > 2 ? c->T[2] + 2 : 1);
+    c->halo_off = (int)((c->smem + 15) / 16 * 16);
+    c->smem = (size_t)c->halo_off + box * 2 * c->D * held_size(c->prec);
+  }
+  if (c->smem > 227 * 1024) return set_err(c, LBM_EINVAL, "tile needs %zu bytes of shared memory (> 227 KB)", c->smem);
   for (int d = 0; d < 3; d++) c->grid[d] = (c->n[d] + c->shift[d] + c->T[d] - 1) / c->T[d];
   return LBM_OK;
 }
@@ -408,7 +422,7 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   const lbm_params &q = *p;
   if (!(q.R >= 1.0) || !(q.omega_g > 0 && q.omega_g < 2) || !(q.omega_l > 0 && q.omega_l < 2) ||
       !(q.omega_alpha > 0 && q.omega_alpha < 2) || q.n_gamma < 1 || q.spalding_mode < 0 || q.spalding_mode > 2 ||
-      !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 3 ||
+      !(q.alpha_floor > 0) || q.g_axis < 0 || q.g_axis >= dim || q.precision < 0 || q.precision > 4 ||
       (q.drag_model != LBM_DRAG_CONST && q.drag_model != LBM_DRAG_CGW) || q.diag_every < 0 ||
       (q.beta_stencil != 0 && q.beta_stencil != 1) || (q.beta_stencil && q.precision == LBM_FP64))
     return LBM_EINVAL;
@@ -442,7 +456,7 @@ int lbm_create(int dim, int lattice, int nx, int ny, int nz, const lbm_params *p
   int rc = choose_tiles(c);
   if (rc) { int e = rc; delete c; return e; }
   const int nsch = q.beta_stencil ? 4 : 6;
-  size_t pop_bytes = (size_t)nsch * c->Q * c->plane * store_size(c->prec);
+  size_t pop_bytes = store_bytes_per_dir(c->prec, nsch) * c->Q * c->plane;
   size_t held_bytes = (size_t)3 * c->plane * held_size(c->prec);
   size_t c_bytes = (size_t)4 * dim * c->plane * held_size(c->prec);
   if (cudaMalloc(&c->pop, pop_bytes) != cudaSuccess || cudaMalloc(&c->held, held_bytes) != cudaSuccess ||
@@ -706,7 +720,7 @@ int lbm_get_diag(lbm_ctx *c, double out[8]) {
 }
 
 int lbm_tile_limit(int lattice, int precision, int *max_threads) {
-  if (lattice < 1 || lattice > 3 || precision < 0 || precision > 3 || !max_threads) return LBM_EINVAL;
+  if (lattice < 1 || lattice > 3 || precision < 0 || precision > 4 || !max_threads) return LBM_EINVAL;
   *max_threads = step_max_threads(lattice, precision);
   return LBM_OK;
 }

@@ -32,6 +32,7 @@ struct lbm_ctx {
   double mass0 = 0.0;
   int T[3] = {1, 1, 1}, shift[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
   size_t smem = 0;
+  int halo_off = 0;  // beta-stencil form: byte offset of the c halo in the step kernel's shared memory
   long long launches = 0;
   // steps replayed from a CUDA graph of one period of the step arguments
   // (lbm_step; lattices whose arguments repeat: no inlet ramp)

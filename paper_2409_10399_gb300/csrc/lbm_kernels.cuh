@@ -68,6 +68,7 @@ struct StepArgs {
   int has_inlet, has_outlet;
   void *cfield;         // beta-stencil form: 2 buffers x 2*D planes of c (held type)
   int beta_own;         // beta-stencil form, first step after init: every q from the node's own c
+  int halo_off;         // beta-stencil form: byte offset of the block's c halo in dynamic shared memory
   int off32;            // Q*plane < 2^32: population offsets fit 32 bits
   // physics
   double invR, R, omega_g, omega_l, omega_a, kgrad;  // kgrad = omega_alpha / cs2
@@ -92,19 +93,29 @@ template <> __device__ __forceinline__ const PhysT<double> &phys<double>(const S
 // ------------------------------------------------------------ store access
 
 template <class S> struct Store;
+// ld / st: the deviation in the arithmetic type; ld_raw: the stored value
+// times `scale` (the step kernel works in those units, see fused_step_node).
 template <> struct Store<double> {
+  static constexpr double scale = 1.0;
   template <class R> __device__ __forceinline__ static R ld(const double *p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static R ld_raw(const double *p) { return (R)__ldg(p); }
   template <class R> __device__ __forceinline__ static void st(double *p, R v) { *p = (double)v; }
 };
 template <> struct Store<float> {
+  static constexpr float scale = 1.0f;
   template <class R> __device__ __forceinline__ static R ld(const float *p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static R ld_raw(const float *p) { return (R)__ldg(p); }
   template <class R> __device__ __forceinline__ static void st(float *p, R v) { *p = (float)v; }
 };
 // Half store of deviations scaled by 2^12 (exact): |f - w r| < 1 < 65504/2^12,
 // and deviations down to 1.5e-8 stay normal numbers (11-bit significand)
-// instead of half subnormals (absolute spacing 6e-8).
+// instead of half subnormals (absolute spacing 6e-8).  The six schemes are
+// stored in pairs (g, l), (alpha_g, alpha_l), (beta_g, beta_l): plane
+// (p*Q + q) of half2 words holds direction q of pair p, so one 32-bit access
+// moves the two schemes of a pair (pop_elem below gives one scheme's half).
 constexpr float HALF_SCALE = 4096.0f, HALF_UNSCALE = 1.0f / 4096.0f;
 template <> struct Store<__half> {
+  static constexpr float scale = HALF_SCALE;
   template <class R> __device__ __forceinline__ static R ld(const __half *p) {
     return (R)(__half2float(__ldg(p)) * HALF_UNSCALE);
   }
@@ -112,6 +123,50 @@ template <> struct Store<__half> {
     *p = __float2half_rn((float)v * HALF_SCALE);
   }
 };
+
+// The FP16AB store: f_g and f_l in float (planes q and Q + q), then the
+// pairs (alpha_g, alpha_l) and (beta_g, beta_l) as half2 words scaled like
+// the half store (planes 2Q + p*Q + q in units of 4 bytes).  The registers
+// hold every population unscaled (scale 1); the half pairs are scaled on
+// load and store.  The tag's size (4) makes the held fields and c float.
+struct MixAB {
+  float tag;
+};
+template <> struct Store<MixAB> {
+  static constexpr float scale = 1.0f;
+};
+
+// Element of scheme s at offset qoff = pq*plane + node of a store of Q*plane
+// elements per scheme (half: the scheme's half of its pair's half2 word).
+template <class S>
+__device__ __forceinline__ S *pop_elem(void *pop, int s, long long qoff, long long Qplane) {
+  if (sizeof(S) == 2) return (S *)pop + ((((long long)(s >> 1)) * Qplane + qoff) << 1) + (s & 1);
+  return (S *)pop + (long long)s * Qplane + qoff;
+}
+// half element of scheme s >= 2 of the FP16AB store
+__device__ __forceinline__ __half *mix_half_elem(void *pop, int s, long long qoff, long long Qplane) {
+  __half *hb = (__half *)((float *)pop + 2 * Qplane);
+  return hb + ((((long long)((s - 2) >> 1)) * Qplane + qoff) << 1) + ((s - 2) & 1);
+}
+// The deviation stored for scheme s at qoff, in double (readout, init).
+template <class S>
+__device__ __forceinline__ double pop_ld(void *pop, int s, long long qoff, long long Qplane) {
+  if constexpr (std::is_same<S, MixAB>::value) {
+    if (s < 2) return (double)__ldg((const float *)pop + (long long)s * Qplane + qoff);
+    return Store<__half>::ld<double>(mix_half_elem(pop, s, qoff, Qplane));
+  } else {
+    return Store<S>::template ld<double>(pop_elem<S>(pop, s, qoff, Qplane));
+  }
+}
+template <class S>
+__device__ __forceinline__ void pop_st(void *pop, int s, long long qoff, long long Qplane, double v) {
+  if constexpr (std::is_same<S, MixAB>::value) {
+    if (s < 2) ((float *)pop)[(long long)s * Qplane + qoff] = (float)v;
+    else Store<__half>::st<double>(mix_half_elem(pop, s, qoff, Qplane), v);
+  } else {
+    Store<S>::template st<double>(pop_elem<S>(pop, s, qoff, Qplane), v);
+  }
+}
 
 // Node geometry: index, offsets (in nodes, 32-bit) of the +1 / -1 neighbour
 // along each axis with periodic wrap, and whether a step leaves the domain
@@ -250,13 +305,31 @@ template <class R> struct Rn;
 template <> struct Rn<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 template <> struct Rn<double> {
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
+
+// v_q . u = s + e exactly: the sum of its at most two nonzero terms
+// (D2Q9, D3Q19 diagonals) as a two-sum, e = 0 along the axes.
+template <class L, class R>
+__device__ __forceinline__ void vdot2(int q, const R u[3], R &s, R &e) {
+  R t[2] = {R(0), R(0)};
+  int n = 0;
+#pragma unroll
+  for (int d = 0; d < L::D; d++) {
+    const int vd = L::v(q, d);
+    if (vd != 0 && n < 2) t[n++] = vd > 0 ? u[d] : -u[d];
+  }
+  s = Rn<R>::add(t[0], t[1]);
+  const R bb = Rn<R>::add(s, -t[0]);
+  e = Rn<R>::add(Rn<R>::add(t[0], -Rn<R>::add(s, -bb)), Rn<R>::add(t[1], -bb));
+}
 
 // f^eq(1, c)_q - w_q of the beta schemes (Eq. (equilibrium) with alpha = 1),
 // in explicitly rounded steps: the six-scheme store evaluates it on the write
@@ -289,14 +362,76 @@ __device__ __forceinline__ void beta_pair(int q, const R cg[3], const R cl[3], R
   bl = beta_dev<L, R>(q, cl);
 }
 
+// Beta-stencil form, step kernel: the block's tile of c (the last step's,
+// buffer 1 - parity) plus a one-node halo, staged once in shared memory, so
+// that the 2*D values of c at every x - v_q come from there instead of global
+// memory.  Node (lx, ly, lz) of the halo box is tile node (lx - 1, ly - 1,
+// lz - 1); components d of c_g at p[d*hn + k], of c_l at p[(D + d)*hn + k].
+struct CHalo {
+  const void *p;  // nullptr: read c from global memory
+  int hx, hy, hn;  // box extent along x, y; nodes in the box
+  int k;           // this thread's node in the box
+};
+
+template <class L, class S, class R>
+__device__ __forceinline__ void halo_c(const CHalo &h, int k, R cg[3], R cl[3]) {
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  const H *p = (const H *)h.p;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    cg[d] = d < L::D ? (R)p[d * h.hn + k] : R(0);
+    cl[d] = d < L::D ? (R)p[(L::D + d) * h.hn + k] : R(0);
+  }
+}
+
+// Fill the block's halo box (all threads of the block; the caller
+// synchronises).  Nodes beyond a non-periodic face are never read (those
+// directions take the face rules) and are left unset.
+template <class L, class S>
+__device__ __forceinline__ void stage_c_halo(const StepArgs &a, void *box, int hx, int hy, int hn, const int o[3],
+                                             int tid, int nthr) {
+  typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
+  const H *cb = (const H *)a.cfield + (long long)(1 - a.parity) * 2 * L::D * a.plane;
+  H *p = (H *)box;
+  // one warp per row of the box (x contiguous), lanes along x
+  const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+  const int rows = hn / hx;
+  for (int r = warp; r < rows; r += nwarp) {
+    int c1 = L::D > 1 ? o[1] - 1 + r % hy : 0, c2 = L::D > 2 ? o[2] - 1 + r / hy : 0;
+    bool ok = true;
+    if (L::D > 1 && (c1 < 0 || c1 >= a.n[1])) {
+      if (a.bc_lo[1] == BC_PERIODIC) c1 = c1 < 0 ? c1 + a.n[1] : c1 - a.n[1];
+      else ok = false;
+    }
+    if (L::D > 2 && (c2 < 0 || c2 >= a.n[2])) {
+      if (a.bc_lo[2] == BC_PERIODIC) c2 = c2 < 0 ? c2 + a.n[2] : c2 - a.n[2];
+      else ok = false;
+    }
+    if (!ok) continue;
+    const long long row = (long long)a.n[0] * (c1 + (long long)a.n[1] * c2);
+    for (int lx = lane; lx < hx; lx += 32) {
+      int c0 = o[0] - 1 + lx;
+      if (c0 < 0 || c0 >= a.n[0]) {
+        if (a.bc_lo[0] != BC_PERIODIC) continue;
+        c0 = c0 < 0 ? c0 + a.n[0] : c0 - a.n[0];
+      }
+      const int k = r * hx + lx;
+#pragma unroll
+      for (int d = 0; d < 2 * L::D; d++) p[d * hn + k] = cb[d * a.plane + row + c0];
+    }
+  }
+}
+
 // Beta-stencil form: the beta deviations arriving at the node along every q,
 // as the six-scheme store would hold them (the write side of the step that
-// produced c, replayed).
+// produced c, replayed); c from the block's halo box when h.p is set.
 template <class L, class S, class R>
-__device__ __forceinline__ void load_beta(const StepArgs &a, const Geo &g, int parity, R fbg[L::Q], R fbl[L::Q]) {
+__device__ __forceinline__ void load_beta(const StepArgs &a, const Geo &g, int parity, R fbg[L::Q], R fbl[L::Q],
+                                          const CHalo &h = CHalo{nullptr, 0, 0, 0, 0}) {
   const int buf = 1 - parity;
   R cg0[3], cl0[3];
-  load_c<L, S, R>(a, buf, g.node, cg0, cl0);
+  if (h.p) halo_c<L, S, R>(h, h.k, cg0, cl0);
+  else load_c<L, S, R>(a, buf, g.node, cg0, cl0);
 #pragma unroll
   for (int q = 0; q < L::Q; q++) {
     const int qo = L::opp(q);
@@ -304,7 +439,10 @@ __device__ __forceinline__ void load_beta(const StepArgs &a, const Geo &g, int p
       beta_pair<L, R>(q, cg0, cl0, fbg[q], fbl[q]);   // initial state: f^eq(1, c(x))
     } else if (!crosses<L>(g, q, -1)) {
       R cg[3], cl[3];
-      load_c<L, S, R>(a, buf, shifted_node<L>(a, g, q, -1), cg, cl);
+      if (h.p)
+        halo_c<L, S, R>(h, h.k - (L::v(q, 0) + h.hx * (L::v(q, 1) + h.hy * L::v(q, 2))), cg, cl);
+      else
+        load_c<L, S, R>(a, buf, shifted_node<L>(a, g, q, -1), cg, cl);
       beta_pair<L, R>(q, cg, cl, fbg[q], fbl[q]);     // streamed from x - v_q
     } else {
       const int rule = face_rule<L>(a, g, qo);          // the rule that sent opp(q) back
@@ -344,24 +482,97 @@ __device__ __forceinline__ const S *scheme_base(const StepArgs &a, int s) {
   return (const S *)a.pop + (long long)(s * L::Q) * a.plane;
 }
 
-// Load all populations of the node (deviations) with the AA read rule (INT:
-// an interior node, see read_slot).
-template <class L, class S, class R, bool BS = false, class OffT = long long, bool INT = false>
-__device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, R f[6][L::Q]) {
-  // the scheme bases formed once, before the loads (left inside the loop
-  // they cost the D2Q9 FP32 step 90 instead of 78 us on the 512 x 2048 box)
-  const S *sb[6];
-#pragma unroll
-  for (int s = 0; s < 6; s++) sb[s] = scheme_base<L, S>(a, s);
-#pragma unroll
-  for (int q = 0; q < L::Q; q++) {
-    int pq;
-    const long long idx = read_slot<L, INT>(a, g, q, parity, pq);
-    const OffT off = pop_offset<L, OffT>(a, pq, idx);
-#pragma unroll
-    for (int s = 0; s < (BS ? 4 : 6); s++) f[s][q] = Store<S>::template ld<R>(sb[s] + off);
+// The node's populations in registers, raw (deviations times
+// Store<S>::scale).  get(s, q): population q of scheme s in the arithmetic
+// type (constant s, q after unrolling).  Float and double stores hold them as
+// R values.  The half store keeps each pair (g, l), (alpha_g, alpha_l),
+// (beta_g, beta_l) packed in one half2 register as loaded (57 registers
+// instead of 114 for D3Q19), converts a value where the collision uses it and
+// sums the moments from the halves directly (moment_sums); in the
+// beta-stencil form the beta values, re-evaluated from c in float, stay
+// float.
+template <class L, class S, class R, bool BS> struct Pops {
+  R f[6][L::Q];
+  __device__ __forceinline__ R get(int s, int q) const { return f[s][q]; }
+};
+template <class L, class R, bool BS> struct Pops<L, MixAB, R, BS> {
+  R f[2][L::Q];
+  __half2 h[BS ? 1 : 2][L::Q];
+  R fb[2][BS ? L::Q : 1];
+  __device__ __forceinline__ R get(int s, int q) const {
+    if (s < 2) return f[s][q];
+    if (BS && s >= 4) return fb[s - 4][q];
+    const __half2 x = h[(s - 2) >> 1][q];
+    return (R)(((s & 1) ? __high2float(x) : __low2float(x)) * HALF_UNSCALE);
   }
-  if (BS) load_beta<L, S, R>(a, g, parity, f[4], f[5]);
+};
+template <class L, class R, bool BS> struct Pops<L, __half, R, BS> {
+  __half2 h[BS ? 2 : 3][L::Q];
+  R fb[2][BS ? L::Q : 1];
+  __device__ __forceinline__ R get(int s, int q) const {
+    if (BS && s >= 4) return fb[s - 4][q];
+    return (R)((s & 1) ? __high2float(h[s >> 1][q]) : __low2float(h[s >> 1][q]));
+  }
+};
+
+// Load all populations of the node with the AA read rule (INT: an interior
+// node, see read_slot), as raw values: deviations times Store<S>::scale.
+template <class L, class S, class R, bool BS = false, class OffT = long long, bool INT = false>
+__device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, Pops<L, S, R, BS> &f,
+                                          const CHalo &h = CHalo{nullptr, 0, 0, 0, 0}) {
+  if constexpr (std::is_same<S, MixAB>::value) {
+    // f_g, f_l from the float planes, the alpha (and beta) pairs as half2
+    const float *gb = (const float *)a.pop;
+    const long long Qp = (long long)L::Q * a.plane;
+    const __half2 *hb = (const __half2 *)(gb + 2 * Qp);
+#pragma unroll
+    for (int q = 0; q < L::Q; q++) {
+      int pq;
+      const long long idx = read_slot<L, INT>(a, g, q, parity, pq);
+      const OffT off = pop_offset<L, OffT>(a, pq, idx);
+      f.f[0][q] = (R)__ldg(gb + off);
+      f.f[1][q] = (R)__ldg(gb + Qp + off);
+#pragma unroll
+      for (int p = 0; p < (BS ? 1 : 2); p++) f.h[p][q] = __ldg(hb + p * Qp + off);
+    }
+    if constexpr (BS) load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
+  } else if constexpr (sizeof(S) == 2) {
+    // half pairs: one 32-bit load per (pair, direction)
+    const __half2 *pb[3];
+#pragma unroll
+    for (int p = 0; p < 3; p++) pb[p] = (const __half2 *)a.pop + (long long)(p * L::Q) * a.plane;
+#pragma unroll
+    for (int q = 0; q < L::Q; q++) {
+      int pq;
+      const long long idx = read_slot<L, INT>(a, g, q, parity, pq);
+      const OffT off = pop_offset<L, OffT>(a, pq, idx);
+#pragma unroll
+      for (int p = 0; p < (BS ? 2 : 3); p++) f.h[p][q] = __ldg(pb[p] + off);
+    }
+    if constexpr (BS) {
+      load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
+#pragma unroll
+      for (int q = 0; q < L::Q; q++) {
+        f.fb[0][q] *= (R)Store<S>::scale;
+        f.fb[1][q] *= (R)Store<S>::scale;
+      }
+    }
+  } else {
+    // the scheme bases formed once, before the loads (left inside the loop
+    // they cost the D2Q9 FP32 step 90 instead of 78 us on the 512 x 2048 box)
+    const S *sb[6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) sb[s] = scheme_base<L, S>(a, s);
+#pragma unroll
+    for (int q = 0; q < L::Q; q++) {
+      int pq;
+      const long long idx = read_slot<L, INT>(a, g, q, parity, pq);
+      const OffT off = pop_offset<L, OffT>(a, pq, idx);
+#pragma unroll
+      for (int s = 0; s < (BS ? 4 : 6); s++) f.f[s][q] = Store<S>::template ld_raw<R>(sb[s] + off);
+    }
+    if (BS) load_beta<L, S, R>(a, g, parity, f.f[4], f.f[5], h);
+  }
 }
 
 // ------------------------------------------------------------- moments
@@ -372,19 +583,94 @@ template <class L, class R> struct Moments {
   R Pg[6], Pl[6];        // Pi - cs2 I, packed xx, yy, zz, xy, xz, yz
   R ag, al, Jg[3], Jl[3];
   R dag, dal;            // a - r (sums of the alpha deviations)
+  R esum;                // sum_q (f_alpha_g + f_alpha_l) deviations: a_g + a_l - (r_g + r_l)
   R Sg, Sl;              // 1 - beta
   R alg, all;            // alpha^B
   R dalg, dall;          // alpha^B - r
+  R cg, cl;              // alpha^B - a, the renormalisation of Eq. (spalding), kept unrounded by a
 };
 
 __host__ __device__ constexpr int pidx(int a, int b) {
   return a == b ? a : ((a + b == 1) ? 3 : ((a + b == 2) ? 4 : 5));
 }
 
-template <class L, class R>
-__device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], Moments<L, R> &m) {
+// Raw sums of the moments in the arithmetic type.  The moving directions
+// are taken in pairs (q, opp q): the first moments sum the pair differences
+// f_q - f_opp(q) and the zeroth and second moments the pair sums.  The even
+// parts of a pair (w (eps - 1), w (alpha - r), the quadratic terms) cancel in
+// the difference before anything is rounded, so a first moment keeps the
+// precision of its own size instead of the spacing of the populations --
+// J = sum v f_alpha is ~1e-3 beside populations of 0.3 w in a gas plume.
+// esum adds f_alpha_g + f_alpha_l direction by direction: the two deviations
+// nearly cancel (alpha_l = 1 - alpha_g), so a_g + a_l - 1 of Eq. (spalding)
+// is formed without the spacing of a_g.  (With double arithmetic and a float
+// store, which rounds no sum, the 2D box stays within 1.2e-7 of the FP64
+// path after 20,000 steps; the plain float sums left 2.7e-5.)
+template <class L, class S, class R, bool BS>
+__device__ __forceinline__ void moment_sums(const Pops<L, S, R, BS> &P, Moments<L, R> &m) {
   constexpr int D = L::D;
-  const PhysT<R> &P = phys<R>(a);
+  m.deg = P.get(0, 0);
+  m.del = P.get(1, 0);
+  m.ag = P.get(2, 0);
+  m.al = P.get(3, 0);
+  m.Sg = -P.get(4, 0);
+  m.Sl = -P.get(5, 0);
+  m.esum = P.get(2, 0) + P.get(3, 0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) m.ug[d] = m.ul[d] = m.Jg[d] = m.Jl[d] = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; k++) m.Pg[k] = m.Pl[k] = R(0);
+#pragma unroll
+  for (int q = 1; q < L::Q; q++) {
+    const int qo = L::opp(q);
+    if (q > qo) continue;
+    R sm[6], df[4];
+#pragma unroll
+    for (int s = 0; s < 6; s++) sm[s] = P.get(s, q) + P.get(s, qo);
+#pragma unroll
+    for (int s = 0; s < 4; s++) df[s] = P.get(s, q) - P.get(s, qo);
+    m.deg += sm[0];
+    m.del += sm[1];
+    m.ag += sm[2];
+    m.al += sm[3];
+    m.Sg -= sm[4];
+    m.Sl -= sm[5];
+    m.esum += (P.get(2, q) + P.get(3, q)) + (P.get(2, qo) + P.get(3, qo));
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      const int vd = L::v(q, d);
+      if (vd != 0) {
+        m.ug[d] += vd * df[0];
+        m.ul[d] += vd * df[1];
+        m.Jg[d] += vd * df[2];
+        m.Jl[d] += vd * df[3];
+      }
+#pragma unroll
+      for (int e = d; e < D; e++) {
+        const int ve = L::v(q, e);
+        if (vd * ve != 0) {
+          m.Pg[pidx(d, e)] += (vd * ve) * sm[0];
+          m.Pl[pidx(d, e)] += (vd * ve) * sm[1];
+        }
+      }
+    }
+  }
+}
+
+// acc +/- x for a half x, in one mixed-precision instruction (sm_100 and
+// later): the exact conversion of x and one rounding, as acc + (float)x.
+__device__ __forceinline__ void hacc(float &acc, __half x, int sign) {
+  const unsigned short b = __half_as_ushort(x);
+  if (sign > 0) asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc) : "h"(b));
+  else asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc) : "h"(b), "h"((unsigned short)0xBC00));  // -1.0
+}
+
+// The same sums from the packed half pairs (same order, same roundings: each
+// term is exact in float, so acc +/- x rounds once as in the float form).
+template <class L, class R, bool BS>
+__device__ __forceinline__ void moment_sums(const Pops<L, __half, R, BS> &P, Moments<L, R> &m) {
+  static_assert(std::is_same<R, float>::value, "the half store computes in float");
+  constexpr int D = L::D;
   m.deg = m.del = m.ag = m.al = m.Sg = m.Sl = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) m.ug[d] = m.ul[d] = m.Jg[d] = m.Jl[d] = R(0);
@@ -392,37 +678,74 @@ __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], M
   for (int k = 0; k < 6; k++) m.Pg[k] = m.Pl[k] = R(0);
 #pragma unroll
   for (int q = 0; q < L::Q; q++) {
-    m.deg += f[0][q];
-    m.del += f[1][q];
-    m.ag += f[2][q];
-    m.al += f[3][q];
-    m.Sg -= f[4][q];
-    m.Sl -= f[5][q];
+    const __half g = __low2half(P.h[0][q]), l = __high2half(P.h[0][q]);
+    const __half ag = __low2half(P.h[1][q]), al = __high2half(P.h[1][q]);
+    hacc(m.deg, g, 1);
+    hacc(m.del, l, 1);
+    hacc(m.ag, ag, 1);
+    hacc(m.al, al, 1);
+    if constexpr (BS) {
+      m.Sg -= P.fb[0][q];
+      m.Sl -= P.fb[1][q];
+    } else {
+      hacc(m.Sg, __low2half(P.h[2][q]), -1);
+      hacc(m.Sl, __high2half(P.h[2][q]), -1);
+    }
 #pragma unroll
     for (int d = 0; d < D; d++) {
-      constexpr int dummy = 0;
-      (void)dummy;
       const int vd = L::v(q, d);
       if (vd != 0) {
-        m.ug[d] += vd * f[0][q];
-        m.ul[d] += vd * f[1][q];
-        m.Jg[d] += vd * f[2][q];
-        m.Jl[d] += vd * f[3][q];
+        hacc(m.ug[d], g, vd);
+        hacc(m.ul[d], l, vd);
+        hacc(m.Jg[d], ag, vd);
+        hacc(m.Jl[d], al, vd);
       }
 #pragma unroll
       for (int e = d; e < D; e++) {
         const int ve = L::v(q, e);
         if (vd * ve != 0) {
-          m.Pg[pidx(d, e)] += (vd * ve) * f[0][q];
-          m.Pl[pidx(d, e)] += (vd * ve) * f[1][q];
+          hacc(m.Pg[pidx(d, e)], g, vd * ve);
+          hacc(m.Pl[pidx(d, e)], l, vd * ve);
         }
       }
+    }
+  }
+}
+
+template <class L, class S, class R, bool BS>
+__device__ __forceinline__ void moments(const StepArgs &a, const Pops<L, S, R, BS> &f, Moments<L, R> &m) {
+  const PhysT<R> &P = phys<R>(a);
+  moment_sums<L>(f, m);
+  // the populations arrive as raw values (times Store<S>::scale, a power of
+  // two): the sums are scaled back exactly
+  constexpr R US = R(1) / (R)Store<S>::scale;
+  if constexpr (sizeof(S) == 2) m.esum = m.ag + m.al;  // unscaled below with them
+  if (US != R(1)) {
+    m.esum *= US;
+    m.deg *= US;
+    m.del *= US;
+    m.ag *= US;
+    m.al *= US;
+    m.Sg *= US;
+    m.Sl *= US;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      m.ug[d] *= US;
+      m.ul[d] *= US;
+      m.Jg[d] *= US;
+      m.Jl[d] *= US;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      m.Pg[k] *= US;
+      m.Pl[k] *= US;
     }
   }
   m.dag = m.ag;
   m.dal = m.al;
   m.ag += P.r_ag;
   m.al += P.r_al;
+  m.cg = m.cl = R(0);
   if (a.spalding == 0) {
     m.alg = m.ag;
     m.all = m.al;
@@ -434,14 +757,23 @@ __device__ __forceinline__ void moments(const StepArgs &a, const R f[6][L::Q], M
     // with e = a_g + a_l - 1 = (a_g - r_g) + (a_l - r_l) + (r_g + r_l - 1), so
     // the small quantities keep their own precision instead of the spacing of
     // alpha^B itself.
+    // The renormalisation itself, alpha^B - a = -a e/(1 + e), is kept as a
+    // number of its own (cg, cl): a few 1e-10 in a gas plume, far below the
+    // spacing of a - r (3e-8 at 0.3), it would vanish if added to a - r in
+    // float, and the alpha equilibria take it separately (collide_all).
     if (m.ag >= R(0) && m.ag <= R(1) && m.al >= R(0) && m.al <= R(1) && m.ag + m.al > R(0)) {
-      const R e = (m.dag + m.dal) + P.rsum1;
-      m.dalg = m.dag - m.ag * (e / (R(1) + e));
+      const R e = m.esum + P.rsum1;
+      const R k = e / (R(1) + e);
+      m.cg = -m.ag * k;
+      m.cl = -m.al * k;
+      m.dalg = m.dag + m.cg;
     } else {
       R Bg = m.ag < R(0) ? R(0) : (m.ag > R(1) ? R(1) : m.ag);
       R Bl = m.al < R(0) ? R(0) : (m.al > R(1) ? R(1) : m.al);
       R sum = Bg + Bl;
       m.dalg = (sum > R(0) ? Bg / sum : R(0.5)) - P.r_ag;
+      m.cg = m.dalg - m.dag;
+      m.cl = (-m.dalg - P.rsum1) - m.dal;
     }
     m.dall = -m.dalg - P.rsum1;  // alpha^B_l = 1 - alpha^B_g
     m.alg = P.r_ag + m.dalg;
@@ -484,11 +816,14 @@ constexpr int XCH = 14;
 // 256 x 1 (249 registers, 8 warps).  The double forms keep 256 threads.
 template <class L, class S> struct StepBounds { static constexpr int threads = 256, blocks = 1; };
 template <> struct StepBounds<Lattice<3>, float> { static constexpr int threads = 128, blocks = 3; };
-template <> struct StepBounds<Lattice<3>, __half> { static constexpr int threads = 128, blocks = 3; };
+template <> struct StepBounds<Lattice<3>, __half> { static constexpr int threads = 128, blocks = 5; };
 template <> struct StepBounds<Lattice<2>, float> { static constexpr int threads = 128, blocks = 5; };
 template <> struct StepBounds<Lattice<2>, __half> { static constexpr int threads = 128, blocks = 5; };
 template <> struct StepBounds<Lattice<1>, float> { static constexpr int threads = 128, blocks = 4; };
 template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads = 128, blocks = 4; };
+template <> struct StepBounds<Lattice<3>, MixAB> { static constexpr int threads = 128, blocks = 4; };
+template <> struct StepBounds<Lattice<2>, MixAB> { static constexpr int threads = 128, blocks = 5; };
+template <> struct StepBounds<Lattice<1>, MixAB> { static constexpr int threads = 128, blocks = 4; };
 
 // One node of the fused step (rows a1-a10).  `a` may live in kernel
 // parameter space (single lattice) or in global memory (batched instances);
@@ -500,10 +835,11 @@ template <> struct StepBounds<Lattice<1>, __half> { static constexpr int threads
 // only), and the inlet/outlet rules are compiled out.
 template <class L, class S, class R, bool BS = false, class OffT = long long, bool IO = true>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
-                                                int latch, bool blk_xch, int gstride, R *xch) {
+                                                int latch, bool blk_xch, int gstride, R *xch,
+                                                const CHalo &halo = CHalo{nullptr, 0, 0, 0, 0}) {
   constexpr int D = L::D, Q = L::Q;
   const int gax = a.g_axis;
-  R f[6][Q];
+  Pops<L, S, R, BS> f;
   Moments<L, R> m;
   R cg[3] = {R(0), R(0), R(0)}, cl[3] = {R(0), R(0), R(0)};
   // interior: no non-periodic face within one step of any node of the warp
@@ -520,9 +856,9 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   }
   interior = SPLIT && __all_sync(__activemask(), interior);
   if (active) {
-    if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f);
-    else load_node<L, S, R, BS, OffT>(a, g, parity, f);
-    moments<L, R>(a, f, m);
+    if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f, halo);
+    else load_node<L, S, R, BS, OffT>(a, g, parity, f, halo);
+    moments<L, S, R, BS>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
       cg[d] = m.all * (m.ug[d] - m.ul[d]);  // Eq. (velocitybeta) with beta = 1
@@ -650,8 +986,12 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
 
   // ---- collisions and AA store with face rules
   const R om_g = P.omega_g, om_l = P.omega_l, om_a = P.omega_a;
+  // f_alpha relaxes to f^eq(alpha^B, u) (Spalding mode 2) or f^eq(a, u):
+  // its even part w [(alpha^B - r) + alpha^B q] is taken as
+  // w [(a - r) + a q] + w c (1 + q) with c = alpha^B - a (0 unless mode 2),
+  // so that c is not lost to the spacing of a - r
   const R aeq_g = a.spalding == 2 ? m.alg : m.ag, aeq_l = a.spalding == 2 ? m.all : m.al;
-  const R deq_g = a.spalding == 2 ? m.dalg : m.dag, deq_l = a.spalding == 2 ? m.dall : m.dal;
+  const R ceq_g = a.spalding == 2 ? m.cg : R(0), ceq_l = a.spalding == 2 ? m.cl : R(0);
   const R rag = P.r_ag, ral = P.r_al;
   // Eq. (eta) for the moving directions: eta_q(phi) = phi, so the offsets of
   // f_I^eq - w are eps_g - 1 (phi_g = 1) and phi eps_l - 1 = dPl, and f_L's
@@ -661,13 +1001,19 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   // w_0 f_L(0) = S - (1 - w_0) psi S; (1 - w_0) x is formed as x - w_0 x so
   // that no rounded 1 - w_0 biases them.
   const R eL_gq = Spp_g * P.psi_g, eL_lq = Spp_l * P.psi_l;
+  // The populations are held and stored in raw units, deviations times
+  // SC = Store<S>::scale (2^12 for the half store, 1 otherwise): every term
+  // of a post-collision population is formed with the weights scaled by SC
+  // (compile-time constants, exact: SC is a power of two), so no population
+  // is rescaled one by one.
+  constexpr R SC = (R)Store<S>::scale;
   const R c2g = BS ? R(0) : beta_c2<L, R>(cg), c2l = BS ? R(0) : beta_c2<L, R>(cl);
 
   // face rules of direction q (walls, Tables 1-2) and its AA store; INTc
   // (std::true_type for interior nodes) compiles them out
   auto finish = [&](const int q, R out[6], auto INTc) {
     constexpr bool INT = decltype(INTc)::value;
-    const R w = wq<L, R>(q);
+    const R w = wq<L, R>(q) * SC;
     const bool cross = !INT && crosses<L>(g, q, +1);
     if (IO && cross) {
       const int rule = face_rule<L>(a, g, q);
@@ -676,16 +1022,16 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         // Table 1: f_g, f_l BB(I) (Eq. (BB): -2 w v.u^B/cs2), f_alpha EQ(S)
         // Dirichlet, f_beta EQ(S) with beta and c extrapolated full-way.
         const R vq = (R)(gax == 0 ? L::v(q, 0) : (gax == 1 ? L::v(q, 1) : L::v(q, 2)));
-        out[0] -= R(2) * aq<L, R>(q) * vq * P.ugIN;
-        out[1] -= R(2) * aq<L, R>(q) * vq * P.ulIN;
+        out[0] -= R(2) * (aq<L, R>(q) * SC) * vq * P.ugIN;
+        out[1] -= R(2) * (aq<L, R>(q) * SC) * vq * P.ulIN;
         R uin[3], lin[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
           uin[d] = d == gax ? P.ugIN : R(0);
           lin[d] = d == gax ? P.ulIN : R(0);
         }
-        out[2] = feqS_dev<L, R>(qo, P.aIN, uin, P.ugIN * P.ugIN, rag);
-        out[3] = feqS_dev<L, R>(qo, R(1) - P.aIN, lin, P.ulIN * P.ulIN, ral);
+        out[2] = SC * feqS_dev<L, R>(qo, P.aIN, uin, P.ugIN * P.ugIN, rag);
+        out[3] = SC * feqS_dev<L, R>(qo, R(1) - P.aIN, lin, P.ulIN * P.ulIN, ral);
         const R *xn = xch + (tid + gstride) * XCH;
         R cb[3] = {R(0), R(0), R(0)}, cc[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -693,7 +1039,11 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
           cb[d] = R(2) * cg[d] - xn[8 + d];
           cc[d] = R(2) * cl[d] - xn[11 + d];
         }
-        if (!BS) beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
+        if (!BS) {
+          beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
+          out[4] *= SC;
+          out[5] *= SC;
+        }
       } else if (rule == BC_OUTLET) {
         // Table 2: f_g, f_l ABB(I) with eps = 1 (so phi = 1) and u EX(hw);
         // f_alpha ABB(S) with alpha, u EX(hw); f_beta EQ(S) with c EX(fw).
@@ -718,16 +1068,36 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         const R abl = R(1.5) * m.all - R(0.5) * xn[7];
         out[2] = -out[2] + R(2) * w * ((abg - rag) + abg * qg);
         out[3] = -out[3] + R(2) * w * ((abl - ral) + abl * ql);
-        if (!BS) beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
+        if (!BS) {
+          beta_pair<L, R>(qo, cb, cc, out[4], out[5]);
+          out[4] *= SC;
+          out[5] *= SC;
+        }
       }
       // BC_WALL: half-way bounce-back keeps out[] as is
     }
     int pq;
     const long long idx = write_slot<L>(a, g, q, cross, parity, pq);
     const OffT off = pop_offset<L, OffT>(a, pq, idx);
+    if constexpr (std::is_same<S, MixAB>::value) {
+      float *gb = (float *)a.pop;
+      const long long Qp = (long long)Q * a.plane;
+      gb[off] = (float)out[0];
+      gb[Qp + off] = (float)out[1];
+      __half2 *hb = (__half2 *)(gb + 2 * Qp);
 #pragma unroll
-    for (int s = 0; s < (BS ? 4 : 6); s++)
-      Store<S>::template st<R>((S *)scheme_base<L, S>(a, s) + off, out[s]);
+      for (int p = 0; p < (BS ? 1 : 2); p++)
+        hb[p * Qp + off] = __floats2half2_rn((float)out[2 + 2 * p] * HALF_SCALE, (float)out[3 + 2 * p] * HALF_SCALE);
+    } else if constexpr (sizeof(S) == 2) {
+      // half pairs: one 32-bit store per pair, both values rounded at once
+#pragma unroll
+      for (int p = 0; p < (BS ? 2 : 3); p++)
+        ((__half2 *)a.pop + (long long)(p * Q) * a.plane)[off] = __floats2half2_rn((float)out[2 * p], (float)out[2 * p + 1]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < (BS ? 4 : 6); s++)
+        Store<S>::template st<R>((S *)scheme_base<L, S>(a, s) + off, out[s]);
+    }
   };
 
   // Collisions, direction by direction: the rest direction alone, the moving
@@ -738,40 +1108,124 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   for (int q = 0; q < Q; q++) {
     const int qo = L::opp(q);
     if (q == 0) {
-      const R w = wq<L, R>(0);
+      const R wu = wq<L, R>(0), w = wu * SC;
       R out[6];
-      const R rest_Il = m.del - (dPl - w * dPl);
-      const R rest_Lg = Spp_g - P.psi_g * (Spp_g - w * Spp_g), rest_Ll = Spp_l - P.psi_l * (Spp_l - w * Spp_l);
-      out[0] = f[0][0] + om_g * (w * (m.deg - R(1.5) * ug2) - f[0][0]) + rest_Lg;
-      out[1] = f[1][0] + om_l * ((rest_Il - w * (R(1.5) * ul2)) - f[1][0]) + rest_Ll;
-      out[2] = f[2][0] + om_a * (feqS_dv<L, R>(0, aeq_g, deq_g, m.ug, ug2) - f[2][0]);
-      out[3] = f[3][0] + om_a * (feqS_dv<L, R>(0, aeq_l, deq_l, m.ul, ul2) - f[3][0]);
-      if (!BS) beta_pair<L, R>(0, cg, cl, out[4], out[5]);
+      typedef Rn<R> O;
+      const R rest_Lg = O::sub(Spp_g, O::mul(P.psi_g, O::fma(-wu, Spp_g, Spp_g)));
+      const R rest_Ll = O::sub(Spp_l, O::mul(P.psi_l, O::fma(-wu, Spp_l, Spp_l)));
+      const R qg0 = O::mul(R(-1.5), ug2), ql0 = O::mul(R(-1.5), ul2);
+      const R f0g = f.get(0, 0), f0l = f.get(1, 0), f0a = f.get(2, 0), f0b = f.get(3, 0);
+      // exact a + b = s + e (two-sum)
+      auto ts = [](R a_, R b_, R &s_, R &e_) {
+        s_ = O::add(a_, b_);
+        const R bb = O::sub(s_, a_);
+        e_ = O::add(O::sub(a_, O::sub(s_, bb)), O::sub(b_, bb));
+      };
+      // The rest direction completes the zeroth moments, with the large
+      // products kept exactly as for the moving directions: f_g's rest
+      // equilibrium w0 [(eps_g - 1) - 3/2 u^2]; f_l's (eps_l - 1) -
+      // (1 - w0)(phi eps_l - 1) - 3/2 w0 u^2 (Eq. (eta) with the weights in
+      // use); f_alpha's w0 [(a - r) - 3/2 a u^2] + w0 c (1 - 3/2 u^2).
+      const R X0g = O::mul(w, m.deg), X0gl = O::add(O::fma(w, m.deg, -X0g), O::mul(w, qg0));
+      out[0] = O::add(f0g, O::fma(om_g, O::add(O::sub(X0g, f0g), X0gl), O::mul(SC, rest_Lg)));
+      R Bh, Be, Ch, Ce;
+      const R Ah = O::mul(wu, dPl), Al = O::fma(wu, dPl, -Ah);  // w0 dPl = Ah + Al
+      ts(dPl, -Ah, Bh, Be);                                    // (1 - w0) dPl = Bh + (Be - Al)
+      ts(m.del, -Bh, Ch, Ce);                                  // rest = Ch + (Ce - (Be - Al))
+      const R X0l = O::mul(SC, Ch), X0ll = O::fma(w, ql0, O::mul(SC, O::sub(Ce, O::sub(Be, Al))));
+      out[1] = O::add(f0l, O::fma(om_l, O::add(O::sub(X0l, f0l), X0ll), O::mul(SC, rest_Ll)));
+      const R X0a = O::mul(w, m.dag), X0b = O::mul(w, m.dal);
+      const R X0al = O::add(O::add(O::fma(w, m.dag, -X0a), O::mul(w, O::mul(m.ag, qg0))),
+                            O::mul(w, O::mul(ceq_g, O::add(R(1), qg0))));
+      const R X0bl = O::add(O::add(O::fma(w, m.dal, -X0b), O::mul(w, O::mul(m.al, ql0))),
+                            O::mul(w, O::mul(ceq_l, O::add(R(1), ql0))));
+      out[2] = O::fma(om_a, O::add(O::sub(X0a, f0a), X0al), f0a);
+      out[3] = O::fma(om_a, O::add(O::sub(X0b, f0b), X0bl), f0b);
+      if (!BS) {
+        beta_pair<L, R>(0, cg, cl, out[4], out[5]);
+        out[4] *= SC;
+        out[5] *= SC;
+      }
       finish(0, out, INTc);
     } else if (q < qo) {
-      const R w = wq<L, R>(q), aw = aq<L, R>(q);
+      // Explicitly rounded operations: the node's arithmetic is compiled into
+      // the interior and the general path, and must give the same bits in
+      // both (no contraction left to the compiler).
+      typedef Rn<R> O;
+      // EX: the exact forms below (the half store, whose populations keep 11
+      // significant bits, gains nothing from them and runs without)
+      constexpr bool EX = !std::is_same<S, __half>::value;
+      const R w = wq<L, R>(q) * SC, aw = aq<L, R>(q) * SC;
       const R vug = vdot<L, R>(q, m.ug), vul = vdot<L, R>(q, m.ul);
       const R vGg = vdot<L, R>(q, Gg), vGl = vdot<L, R>(q, Gl);
-      const R qug = R(4.5) * vug * vug - R(1.5) * ug2, qul = R(4.5) * vul * vul - R(1.5) * ul2;
-      // f_g, f_l: even / odd parts of f_I^eq - w and of f_L
-      const R Xg = w * (m.deg + qug), Yg = aw * vug, Xl = w * (dPl + qul), Yl = aw * vul;
-      const R Fg = w * eL_gq, Hg = aw * vGg, Fl = w * eL_lq, Hl = aw * vGl;
-      // f_alpha (the split of feqS_dv)
-      const R Xag = w * (deq_g + aeq_g * qug), Yag = aeq_g * (aw * vug);
-      const R Xal = w * (deq_l + aeq_l * qul), Yal = aeq_l * (aw * vul);
+      const R qug = O::fma(O::mul(R(4.5), vug), vug, O::mul(R(-1.5), ug2));
+      const R qul = O::fma(O::mul(R(4.5), vul), vul, O::mul(R(-1.5), ul2));
+      // Even parts of f_I^eq - w (f_g, f_l) and of f^eq(alpha, u) - w r:
+      // the large product w d (d = eps_g - 1, phi eps_l - 1, a - r) is kept
+      // exactly as hi + lo, lo = fma(w, d, -hi), so that the equilibrium's
+      // zeroth moment, sum_q w_q d = d (the float weights sum to 1 exactly),
+      // is not biased by the rounding of the products.  The roundings of w d
+      // are deterministic in the state and do not cancel over the
+      // directions; in a slowly varying state they moved eps and alpha the
+      // same way every step.
+      const R Xg = O::mul(w, m.deg), Xgl = EX ? O::add(O::fma(w, m.deg, -Xg), O::mul(w, qug)) : O::mul(w, qug);
+      const R Xl = O::mul(w, dPl), Xll = EX ? O::add(O::fma(w, dPl, -Xl), O::mul(w, qul)) : O::mul(w, qul);
+      // Odd parts a_q (v . u) of f_g, f_l, formed exactly as hi + lo (v . u
+      // as a two-sum of its at most two nonzero terms, the product as a
+      // two-product), so that the equilibrium's first moment,
+      // sum_q v_q a_q (v_q . u) = u, is exactly the u the moments gave: the
+      // collision then adds no momentum of its own.  A rounded first moment
+      // acts as a small force every step; on the liquid, whose momentum the
+      // interphase force restores only at 1/R of the gas's rate (Eq. (Gl)),
+      // it left u_l 1.5e-5 from the FP64 path after 20,000 steps of the 2D
+      // box.
+      R vgs = vug, vge = R(0), vls = vul, vle = R(0);
+      if constexpr (EX) {
+        vdot2<L, R>(q, m.ug, vgs, vge);
+        vdot2<L, R>(q, m.ul, vls, vle);
+      }
+      const R Yg = O::mul(aw, vgs), Ygl = EX ? O::fma(aw, vge, O::fma(aw, vgs, -Yg)) : R(0);
+      const R Yl = O::mul(aw, vls), Yll = EX ? O::fma(aw, vle, O::fma(aw, vls, -Yl)) : R(0);
+      const R Fg = O::mul(w, eL_gq), Hg = O::mul(aw, vGg), Fl = O::mul(w, eL_lq), Hl = O::mul(aw, vGl);
+      // f_alpha: alpha^B = a + c (c the renormalisation, Spalding mode 2)
+      const R Xag = O::mul(w, m.dag), Xal = O::mul(w, m.dal);
+      const R Xagl = O::add(O::add(EX ? O::fma(w, m.dag, -Xag) : R(0), O::mul(w, O::mul(m.ag, qug))),
+                            O::mul(w, O::mul(ceq_g, O::add(R(1), qug))));
+      const R Xall = O::add(O::add(EX ? O::fma(w, m.dal, -Xal) : R(0), O::mul(w, O::mul(m.al, qul))),
+                            O::mul(w, O::mul(ceq_l, O::add(R(1), qul))));
+      const R Yag = O::mul(aeq_g, O::mul(aw, vug)), Yal = O::mul(aeq_l, O::mul(aw, vul));
+      // f* = f + [omega (f^eq - f) + forcing], f^eq - f = (X_hi - f) + X_lo +- Y
+      // formed without losing the smaller terms: X_hi - f is taken exactly as
+      // s + e (Knuth's two-sum), then (s +- Y) + (e + X_lo).  Whichever of the
+      // even part X and the odd part Y (the flux) carries f, s +- Y cancels it
+      // exactly and the rest enters at its own precision; the node's value is
+      // rounded once more, at the spacing of f.  (Grouped as (X +- Y) - f, the
+      // smaller part was quantised to the spacing of the larger one every
+      // step.)  For f_alpha the even part w (alpha - r) always carries f
+      // (~0.29 w in a gas plume) and X_hi - f cancels exactly without the
+      // two-sum.
+      const R fg = f.get(0, q), fgo = f.get(0, qo), fl = f.get(1, q), flo = f.get(1, qo);
+      const R fa = f.get(2, q), fao = f.get(2, qo), fb = f.get(3, q), fbo = f.get(3, qo);
+      auto neq = [](R Xh, R Xlo, R fv, R Y) {  // (Xh - fv) + Xlo + Y, Xh - fv as the exact s + e
+        const R s = O::sub(Xh, fv);
+        if constexpr (!EX) return O::add(O::add(s, Y), Xlo);
+        const R bb = O::sub(s, Xh);
+        const R e = O::sub(O::sub(Xh, O::sub(s, bb)), O::add(fv, bb));
+        return O::add(O::add(s, Y), O::add(e, Xlo));
+      };
       R oa[6], ob[6];
-      oa[0] = f[0][q] + om_g * ((Xg + Yg) - f[0][q]) + (Fg + Hg);
-      ob[0] = f[0][qo] + om_g * ((Xg - Yg) - f[0][qo]) + (Fg - Hg);
-      oa[1] = f[1][q] + om_l * ((Xl + Yl) - f[1][q]) + (Fl + Hl);
-      ob[1] = f[1][qo] + om_l * ((Xl - Yl) - f[1][qo]) + (Fl - Hl);
-      oa[2] = f[2][q] + om_a * ((Xag + Yag) - f[2][q]);
-      ob[2] = f[2][qo] + om_a * ((Xag - Yag) - f[2][qo]);
-      oa[3] = f[3][q] + om_a * ((Xal + Yal) - f[3][q]);
-      ob[3] = f[3][qo] + om_a * ((Xal - Yal) - f[3][qo]);
+      oa[0] = O::add(fg, O::fma(om_g, neq(Xg, O::add(Xgl, Ygl), fg, Yg), O::add(Fg, Hg)));
+      ob[0] = O::add(fgo, O::fma(om_g, neq(Xg, O::sub(Xgl, Ygl), fgo, -Yg), O::sub(Fg, Hg)));
+      oa[1] = O::add(fl, O::fma(om_l, neq(Xl, O::add(Xll, Yll), fl, Yl), O::add(Fl, Hl)));
+      ob[1] = O::add(flo, O::fma(om_l, neq(Xl, O::sub(Xll, Yll), flo, -Yl), O::sub(Fl, Hl)));
+      oa[2] = O::fma(om_a, O::add(O::add(O::sub(Xag, fa), Xagl), Yag), fa);
+      ob[2] = O::fma(om_a, O::sub(O::add(O::sub(Xag, fao), Xagl), Yag), fao);
+      oa[3] = O::fma(om_a, O::add(O::add(O::sub(Xal, fb), Xall), Yal), fb);
+      ob[3] = O::fma(om_a, O::sub(O::add(O::sub(Xal, fbo), Xall), Yal), fbo);
       if (!BS) {
         // beta_dev of q and opp(q) from one even part (v_opp . c = -v_q . c exactly)
         R vcg, vcl;
-        const R xg = beta_even<L, R>(q, cg, c2g, vcg), xl = beta_even<L, R>(q, cl, c2l, vcl);
+        const R xg = beta_even<L, R>(q, cg, c2g, vcg) * SC, xl = beta_even<L, R>(q, cl, c2l, vcl) * SC;
         oa[4] = Rn<R>::fma(aw, vcg, xg);
         ob[4] = Rn<R>::fma(aw, -vcg, xg);
         oa[5] = Rn<R>::fma(aw, vcl, xl);
@@ -805,7 +1259,19 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
   const bool blk_xch = IO && ((a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng));
-  fused_step_node<L, S, R, BS, OffT, IO>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch);
+  CHalo halo{nullptr, 0, 0, 0, 0};
+  if constexpr (BS) {
+    // the block's c tile plus a one-node halo, from the last step's buffer
+    const int hx = a.T[0] + 2, hy = L::D > 1 ? a.T[1] + 2 : 1, hz = L::D > 2 ? a.T[2] + 2 : 1;
+    const int o[3] = {(int)blockIdx.x * a.T[0] - a.shift[0], (int)blockIdx.y * a.T[1] - a.shift[1],
+                      (int)blockIdx.z * a.T[2] - a.shift[2]};
+    void *box = smem_raw + a.halo_off;
+    stage_c_halo<L, S>(a, box, hx, hy, hx * hy * hz, o, tid, a.T[0] * a.T[1] * a.T[2]);
+    __syncthreads();
+    const int k = (threadIdx.x + 1) + hx * ((L::D > 1 ? threadIdx.y + 1 : 0) + hy * (L::D > 2 ? threadIdx.z + 1 : 0));
+    halo = CHalo{box, hx, hy, hx * hy * hz, k};
+  }
+  fused_step_node<L, S, R, BS, OffT, IO>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch, halo);
 }
 
 // Batched form: one launch advances many independent lattices (instances) of
@@ -906,10 +1372,10 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
     g.c[1] = (int)((i / a.n[0]) % a.n[1]);
     g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
     make_geo(a, D, g);
-    R f[6][Q];
+    Pops<L, S, R, BS> f;
     load_node<L, S, R, BS>(a, g, a.parity, f);
     Moments<L, R> m;
-    moments<L, R>(a, f, m);
+    moments<L, S, R, BS>(a, f, m);
     if (mode & 1) {
       double *o = ma.out;
       const long long N = ma.N;
@@ -927,7 +1393,7 @@ __global__ void __launch_bounds__(256) k_moments(const MomArgs ma, int mode) {
 #pragma unroll
       for (int s = 0; s < 6; s++)
 #pragma unroll
-        for (int q = 0; q < Q; q++) bad = bad || !isfinite((double)f[s][q]);
+        for (int q = 0; q < Q; q++) bad = bad || !isfinite((double)f.get(s, q));
       double ug2 = 0, ul2 = 0;
       for (int d = 0; d < D; d++) {
         ug2 += (double)m.ug[d] * (double)m.ug[d];
@@ -964,7 +1430,6 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
   g.c[1] = (int)((i / a.n[0]) % a.n[1]);
   g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
   make_geo(a, D, g);
-  const S *base = (const S *)a.pop;
   // the references the step kernel adds (in its arithmetic type)
   const double rg = sizeof(S) == 8 ? a.r_ag : (double)a.pf.r_ag, rl = sizeof(S) == 8 ? a.r_al : (double)a.pf.r_al;
   const double r = a.plain ? 0.0 : (s == 2 ? rg : (s == 3 ? rl : 1.0));
@@ -979,7 +1444,7 @@ __global__ void __launch_bounds__(256) k_pops(const MomArgs ma, int s) {
   for (int q = 0; q < Q; q++) {
     int pq;
     long long idx = read_slot<L>(a, g, q, a.parity, pq);
-    double dv = Store<S>::template ld<double>(base + (long long)(s * Q + pq) * a.plane + idx);
+    double dv = pop_ld<S>(a.pop, s, (long long)pq * a.plane + idx, Q * a.plane);
     ma.out[(long long)q * ma.N + i] = a.plain ? dv : dv + L::w(q) * r;
   }
 }
@@ -1012,7 +1477,6 @@ __global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *al
     ug2 += ug[d] * ug[d];
     ul2 += ul[d] * ul[d];
   }
-  S *base = (S *)a.pop;
   // c in the step kernel's arithmetic type H, and the beta equilibria from
   // it as that kernel evaluates them (beta_dev), so the beta-stencil form,
   // which starts from the same c, sees the same initial beta populations
@@ -1037,7 +1501,7 @@ __global__ void __launch_bounds__(256) k_init(const MomArgs ma, const double *al
     o[5] = (double)beta_dev<L, H>(q, clH);
 #pragma unroll
     for (int s = 0; s < (BS ? 4 : 6); s++)
-      Store<S>::template st<double>(base + (long long)(s * Q + q) * a.plane + i, o[s]);
+      pop_st<S>(a.pop, s, (long long)q * a.plane + i, Q * a.plane, o[s]);
   }
   if (BS) {
     // beta-stencil form: c of the initial state in the buffer the first step

@@ -146,12 +146,13 @@ __global__ void __launch_bounds__(256) k_step_ref(const StepArgs a) {
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
   const bool blk_xch = (a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng);
 
-  double f[6][Q];
+  Pops<L, double, double, false> P;  // full FP64 populations (plain store)
+  double (&f)[6][Q] = P.f;
   RefMom m;
   double c_g[3] = {0.0, 0.0, 0.0}, c_l[3] = {0.0, 0.0, 0.0};
   if (active) {
     make_geo(a, D, g);
-    load_node<L, double, double>(a, g, a.parity, f);
+    load_node<L, double, double>(a, g, a.parity, P);
     ref_moments<L>(a, f, m);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -387,8 +388,9 @@ __global__ void __launch_bounds__(256) k_moments_ref(const MomArgs ma, int mode)
     g.c[1] = (int)((i / a.n[0]) % a.n[1]);
     g.c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
     make_geo(a, D, g);
-    double f[6][Q];
-    load_node<L, double, double>(a, g, a.parity, f);
+    Pops<L, double, double, false> P;  // full FP64 populations (plain store)
+    double (&f)[6][Q] = P.f;
+    load_node<L, double, double>(a, g, a.parity, P);
     RefMom m;
     ref_moments<L>(a, f, m);
     if (mode & 1) {

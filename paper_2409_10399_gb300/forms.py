@@ -11,9 +11,9 @@ the workload's stated step count (or at the reduced size the workload names
 for its error study), per field: alpha_g, u_g, u_l, p_k - 1/3.
 
 - box2d (D2Q9 512 x 2048, inlet strip, 20,000 steps): FP32 (the benchmark
-  form), FP16-dev, FP64.
+  form), FP16-dev, FP16AB, FP64.
 - column3d (D3Q19 256 x 256 x 512, 5,000 steps; errors at 64 x 64 x 128):
-  FP16-dev (its form), FP32, FP64.
+  FP16-dev (its form), FP16AB (f_g, f_l float), FP32, FP64.
 - batch256 (256 ragged D2Q9 FP32 columns, 1.06e8 nodes): one launch per step
   under graph replay, against the same instances stepped one by one with the
   FP32 and FP64 single-lattice path; accuracy of one instance against its
@@ -41,12 +41,14 @@ from . import params as lparams
 
 # FP64 operations executed per node update by the FP64 reference step
 # kernel (k_step_ref), counted with ncu as dadd + dmul + 2 dfma over the
-# threads of one launch on the lattice's workload recipe, divided by the nodes;
-# None where not counted.
-FP64_OPS_PER_NODE = {"D1Q3": None, "D2Q9": None, "D3Q19": None}
+# threads of a launch without the lag latch on the lattice's workload recipe
+# (column1d 512, box2d at 512 x 256, column3d at 64 x 64 x 128), divided by the
+# nodes.  The dfma come mostly from the IEEE division and square root
+# sequences: the reference evaluates the paper's divisions literally.
+FP64_OPS_PER_NODE = {"D1Q3": 710, "D2Q9": 1956, "D3Q19": 4219}
 B6 = {("D2Q9", "fp32"): 444, ("D2Q9", "fp16dev"): 228, ("D2Q9", "fp64"): 888,
       ("D3Q19", "fp32"): 924, ("D3Q19", "fp16dev"): 468, ("D3Q19", "fp64"): 1848,
-      ("D1Q3", "fp64"): 312, ("D1Q3", "fp32"): 156}
+      ("D1Q3", "fp64"): 312, ("D1Q3", "fp32"): 156, ("D2Q9", "fp16ab"): 300, ("D3Q19", "fp16ab"): 620}
 
 
 def _torch():
@@ -144,12 +146,12 @@ def box2d(stream, quick=False):
     w = lbm_inputs.WORKLOADS["box2d"]
     lat, dims = w["lattice"], w["dims"]
     res = dict(workload="box2d D2Q9 512x2048, R=1000, inlet strip", nodes=int(np.prod(dims)))
-    res["forms"] = _lattice_forms("box2d", lat, dims, ("fp32", "fp16dev", "fp64"), 400, stream)
+    res["forms"] = _lattice_forms("box2d", lat, dims, ("fp32", "fp16dev", "fp16ab", "fp64"), 400, stream)
     steps = 2000 if quick else w["steps"]
     f = lbm_inputs.fields_for("box2d")
     ref, _ = run(lat, dims, lparams.lattice_params(w["physics"], precision="fp64"), f, steps, stream)
     acc = {}
-    for prec in ("fp32", "fp16dev"):
+    for prec in ("fp32", "fp16dev", "fp16ab"):
         got, d = run(lat, dims, lparams.lattice_params(w["physics"], precision=prec), f, steps, stream)
         acc[prec] = dict(errors(got, ref, w["physics"]["R"]), nonfinite_nodes=int(d[5]))
     res["accuracy"] = dict(against="fp64 GPU path, same state", steps=steps, dims=list(dims), **acc)
@@ -161,13 +163,13 @@ def column3d(stream, quick=False):
     w = lbm_inputs.WORKLOADS["column3d"]
     lat, dims = w["lattice"], w["dims"]
     res = dict(workload="column3d D3Q19 256x256x512, R=1000, walls x/y, periodic z", nodes=int(np.prod(dims)))
-    res["forms"] = _lattice_forms("column3d", lat, dims, ("fp16dev", "fp32", "fp64"), 50, stream)
+    res["forms"] = _lattice_forms("column3d", lat, dims, ("fp16dev", "fp16ab", "fp32", "fp64"), 50, stream)
     small = (64, 64, 128)
     steps = 500 if quick else w["steps"]
     f = lbm_inputs.fields_for("column3d", dims=small)
     ref, _ = run(lat, small, lparams.lattice_params(w["physics"], precision="fp64"), f, steps, stream)
     acc = {}
-    for prec in ("fp16dev", "fp32"):
+    for prec in ("fp16dev", "fp16ab", "fp32"):
         got, d = run(lat, small, lparams.lattice_params(w["physics"], precision=prec), f, steps, stream)
         acc[prec] = dict(errors(got, ref, w["physics"]["R"]), nonfinite_nodes=int(d[5]))
     res["accuracy"] = dict(against="fp64 GPU path, same state", steps=steps, dims=list(small), **acc)
