@@ -603,9 +603,9 @@ __host__ __device__ constexpr int pidx(int a, int b) {
 // J = sum v f_alpha is ~1e-3 beside populations of 0.3 w in a gas plume.
 // esum adds f_alpha_g + f_alpha_l direction by direction: the two deviations
 // nearly cancel (alpha_l = 1 - alpha_g), so a_g + a_l - 1 of Eq. (spalding)
-// is formed without the spacing of a_g.  (With double arithmetic and a float
-// store, which rounds no sum, the 2D box stays within 1.2e-7 of the FP64
-// path after 20,000 steps; the plain float sums left 2.7e-5.)
+// is formed without the spacing of a_g.  (The rounding of the zeroth sums
+// does not move mass: the collision's rest direction takes the remainder,
+// see collide_all.)
 template <class L, class S, class R, bool BS>
 __device__ __forceinline__ void moment_sums(const Pops<L, S, R, BS> &P, Moments<L, R> &m) {
   constexpr int D = L::D;
@@ -995,11 +995,12 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
   const R rag = P.r_ag, ral = P.r_al;
   // Eq. (eta) for the moving directions: eta_q(phi) = phi, so the offsets of
   // f_I^eq - w are eps_g - 1 (phi_g = 1) and phi eps_l - 1 = dPl, and f_L's
-  // is S psi.  The rest direction takes what makes the zeroth moments exact
-  // with the weights in use (sum w_q = 1): w_0 eta_0 = 1 - (1 - w_0) phi, i.e.
-  // w_0 f_I^eq(0) - w_0 = (eps_l - 1) - (1 - w_0) dPl for the liquid, and
-  // w_0 f_L(0) = S - (1 - w_0) psi S; (1 - w_0) x is formed as x - w_0 x so
-  // that no rounded 1 - w_0 biases them.
+  // is S psi.  The rest direction's takes what makes the zeroth moments
+  // exact with the weights in use (sum w_q = 1): w_0 eta_0 = 1 - (1 - w_0)
+  // phi, so its f_I^eq is the remainder of the moving directions' (taken as
+  // such by the rest direction's collision below), and w_0 f_L(0) = S -
+  // (1 - w_0) psi S, (1 - w_0) x formed as x - w_0 x so that no rounded
+  // 1 - w_0 biases it.
   const R eL_gq = Spp_g * P.psi_g, eL_lq = Spp_l * P.psi_l;
   // The populations are held and stored in raw units, deviations times
   // SC = Store<S>::scale (2^12 for the half store, 1 otherwise): every term
@@ -1100,54 +1101,60 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
     }
   };
 
-  // Collisions, direction by direction: the rest direction alone, the moving
-  // ones in pairs (q, opp q), whose equilibria share their even part
-  // w_q (...) and differ in the sign of their odd part a_q v_q . u.
+  // Collisions, direction by direction: the moving ones in pairs (q, opp q),
+  // whose equilibria share their even part w_q (...) and differ in the sign
+  // of their odd part a_q v_q . u; the rest direction last.  The rest
+  // direction's non-equilibrium part is not formed from its own equilibrium
+  // but as what makes sum_q (f^eq_q - f_q) exactly the change the collision
+  // must make -- zero for f_g and f_l (the source S'' enters through the
+  // forcing), Spalding's c for f_alpha -- given the moving directions' parts
+  // as computed (nsum: small numbers, summed with small rounding).  In exact
+  // arithmetic the two are the same (the equilibria's zeroth moments are the
+  // moments').  So the collision conserves mass whatever the rounding of the
+  // zeroth moment sums, and the correction goes where it changes no higher
+  // moment (v_0 = 0).  Without it, the sums' rounding moved mass the same
+  // way every step in a slowly varying state (the batched sweep's columns,
+  // gas below liquid, drifted 8e-6 in gas volume and 6e-5 in gas momentum
+  // over 10,000 steps).
+  // The rest direction's four populations wait in shared memory through the
+  // pair loop where the kernel is short of registers (the FP32 store: four
+  // live registers fewer, so fewer spills inside the loop), a slot per thread.
+  constexpr bool STASH = std::is_same<S, float>::value && std::is_same<R, float>::value;
+  constexpr int NST = StepBounds<L, S>::threads;
+  __shared__ R rest_stash[STASH ? 4 * NST : 1];
+  volatile R *const stash = rest_stash + (STASH ? threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z) : 0);
+  auto rest_f = [&](int s) -> R {
+    if constexpr (STASH) return stash[s * NST];
+    else return f.get(s, 0);
+  };
+  auto collide_rest = [&](const R nsum[4], auto INTc) {
+    typedef Rn<R> O;
+    const R wu = wq<L, R>(0);
+    R out[6];
+    const R rest_Lg = O::sub(Spp_g, O::mul(P.psi_g, O::fma(-wu, Spp_g, Spp_g)));
+    const R rest_Ll = O::sub(Spp_l, O::mul(P.psi_l, O::fma(-wu, Spp_l, Spp_l)));
+    out[0] = O::add(rest_f(0), O::fma(om_g, -nsum[0], O::mul(SC, rest_Lg)));
+    out[1] = O::add(rest_f(1), O::fma(om_l, -nsum[1], O::mul(SC, rest_Ll)));
+    out[2] = O::fma(om_a, O::sub(O::mul(SC, ceq_g), nsum[2]), rest_f(2));
+    out[3] = O::fma(om_a, O::sub(O::mul(SC, ceq_l), nsum[3]), rest_f(3));
+    if (!BS) {
+      beta_pair<L, R>(0, cg, cl, out[4], out[5]);
+      out[4] *= SC;
+      out[5] *= SC;
+    }
+    finish(0, out, INTc);
+  };
+
   auto collide_all = [&](auto INTc) {
+  R nsum[4] = {R(0), R(0), R(0), R(0)};  // sum over the moving directions of f^eq - f
+  if constexpr (STASH) {
 #pragma unroll
-  for (int q = 0; q < Q; q++) {
+    for (int s = 0; s < 4; s++) stash[s * NST] = f.get(s, 0);
+  }
+#pragma unroll
+  for (int q = 1; q < Q; q++) {
     const int qo = L::opp(q);
-    if (q == 0) {
-      const R wu = wq<L, R>(0), w = wu * SC;
-      R out[6];
-      typedef Rn<R> O;
-      const R rest_Lg = O::sub(Spp_g, O::mul(P.psi_g, O::fma(-wu, Spp_g, Spp_g)));
-      const R rest_Ll = O::sub(Spp_l, O::mul(P.psi_l, O::fma(-wu, Spp_l, Spp_l)));
-      const R qg0 = O::mul(R(-1.5), ug2), ql0 = O::mul(R(-1.5), ul2);
-      const R f0g = f.get(0, 0), f0l = f.get(1, 0), f0a = f.get(2, 0), f0b = f.get(3, 0);
-      // exact a + b = s + e (two-sum)
-      auto ts = [](R a_, R b_, R &s_, R &e_) {
-        s_ = O::add(a_, b_);
-        const R bb = O::sub(s_, a_);
-        e_ = O::add(O::sub(a_, O::sub(s_, bb)), O::sub(b_, bb));
-      };
-      // The rest direction completes the zeroth moments, with the large
-      // products kept exactly as for the moving directions: f_g's rest
-      // equilibrium w0 [(eps_g - 1) - 3/2 u^2]; f_l's (eps_l - 1) -
-      // (1 - w0)(phi eps_l - 1) - 3/2 w0 u^2 (Eq. (eta) with the weights in
-      // use); f_alpha's w0 [(a - r) - 3/2 a u^2] + w0 c (1 - 3/2 u^2).
-      const R X0g = O::mul(w, m.deg), X0gl = O::add(O::fma(w, m.deg, -X0g), O::mul(w, qg0));
-      out[0] = O::add(f0g, O::fma(om_g, O::add(O::sub(X0g, f0g), X0gl), O::mul(SC, rest_Lg)));
-      R Bh, Be, Ch, Ce;
-      const R Ah = O::mul(wu, dPl), Al = O::fma(wu, dPl, -Ah);  // w0 dPl = Ah + Al
-      ts(dPl, -Ah, Bh, Be);                                    // (1 - w0) dPl = Bh + (Be - Al)
-      ts(m.del, -Bh, Ch, Ce);                                  // rest = Ch + (Ce - (Be - Al))
-      const R X0l = O::mul(SC, Ch), X0ll = O::fma(w, ql0, O::mul(SC, O::sub(Ce, O::sub(Be, Al))));
-      out[1] = O::add(f0l, O::fma(om_l, O::add(O::sub(X0l, f0l), X0ll), O::mul(SC, rest_Ll)));
-      const R X0a = O::mul(w, m.dag), X0b = O::mul(w, m.dal);
-      const R X0al = O::add(O::add(O::fma(w, m.dag, -X0a), O::mul(w, O::mul(m.ag, qg0))),
-                            O::mul(w, O::mul(ceq_g, O::add(R(1), qg0))));
-      const R X0bl = O::add(O::add(O::fma(w, m.dal, -X0b), O::mul(w, O::mul(m.al, ql0))),
-                            O::mul(w, O::mul(ceq_l, O::add(R(1), ql0))));
-      out[2] = O::fma(om_a, O::add(O::sub(X0a, f0a), X0al), f0a);
-      out[3] = O::fma(om_a, O::add(O::sub(X0b, f0b), X0bl), f0b);
-      if (!BS) {
-        beta_pair<L, R>(0, cg, cl, out[4], out[5]);
-        out[4] *= SC;
-        out[5] *= SC;
-      }
-      finish(0, out, INTc);
-    } else if (q < qo) {
+    if (q < qo) {
       // Explicitly rounded operations: the node's arithmetic is compiled into
       // the interior and the general path, and must give the same bits in
       // both (no contraction left to the compiler).
@@ -1168,7 +1175,8 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
       // are deterministic in the state and do not cancel over the
       // directions; in a slowly varying state they moved eps and alpha the
       // same way every step.
-      const R Xg = O::mul(w, m.deg), Xgl = EX ? O::add(O::fma(w, m.deg, -Xg), O::mul(w, qug)) : O::mul(w, qug);
+      const R Xg = O::mul(w, m.deg);
+      const R Xgl = EX ? O::add(O::fma(w, m.deg, -Xg), O::mul(w, qug)) : O::mul(w, qug);
       const R Xl = O::mul(w, dPl), Xll = EX ? O::add(O::fma(w, dPl, -Xl), O::mul(w, qul)) : O::mul(w, qul);
       // Odd parts a_q (v . u) of f_g, f_l, formed exactly as hi + lo (v . u
       // as a two-sum of its at most two nonzero terms, the product as a
@@ -1184,8 +1192,10 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         vdot2<L, R>(q, m.ug, vgs, vge);
         vdot2<L, R>(q, m.ul, vls, vle);
       }
-      const R Yg = O::mul(aw, vgs), Ygl = EX ? O::fma(aw, vge, O::fma(aw, vgs, -Yg)) : R(0);
-      const R Yl = O::mul(aw, vls), Yll = EX ? O::fma(aw, vle, O::fma(aw, vls, -Yl)) : R(0);
+      const R Yg = O::mul(aw, vgs);
+      const R Ygl = EX ? O::fma(aw, vge, O::fma(aw, vgs, -Yg)) : R(0);
+      const R Yl = O::mul(aw, vls);
+      const R Yll = EX ? O::fma(aw, vle, O::fma(aw, vls, -Yl)) : R(0);
       const R Fg = O::mul(w, eL_gq), Hg = O::mul(aw, vGg), Fl = O::mul(w, eL_lq), Hl = O::mul(aw, vGl);
       // f_alpha: alpha^B = a + c (c the renormalisation, Spalding mode 2)
       const R Xag = O::mul(w, m.dag), Xal = O::mul(w, m.dal);
@@ -1213,15 +1223,21 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
         const R e = O::sub(O::sub(Xh, O::sub(s, bb)), O::add(fv, bb));
         return O::add(O::add(s, Y), O::add(e, Xlo));
       };
+      const R ta[4] = {neq(Xg, O::add(Xgl, Ygl), fg, Yg), neq(Xl, O::add(Xll, Yll), fl, Yl),
+                       O::add(O::add(O::sub(Xag, fa), Xagl), Yag), O::add(O::add(O::sub(Xal, fb), Xall), Yal)};
+      const R tb[4] = {neq(Xg, O::sub(Xgl, Ygl), fgo, -Yg), neq(Xl, O::sub(Xll, Yll), flo, -Yl),
+                       O::sub(O::add(O::sub(Xag, fao), Xagl), Yag), O::sub(O::add(O::sub(Xal, fbo), Xall), Yal)};
+#pragma unroll
+      for (int s = 0; s < 4; s++) nsum[s] = O::add(nsum[s], O::add(ta[s], tb[s]));
       R oa[6], ob[6];
-      oa[0] = O::add(fg, O::fma(om_g, neq(Xg, O::add(Xgl, Ygl), fg, Yg), O::add(Fg, Hg)));
-      ob[0] = O::add(fgo, O::fma(om_g, neq(Xg, O::sub(Xgl, Ygl), fgo, -Yg), O::sub(Fg, Hg)));
-      oa[1] = O::add(fl, O::fma(om_l, neq(Xl, O::add(Xll, Yll), fl, Yl), O::add(Fl, Hl)));
-      ob[1] = O::add(flo, O::fma(om_l, neq(Xl, O::sub(Xll, Yll), flo, -Yl), O::sub(Fl, Hl)));
-      oa[2] = O::fma(om_a, O::add(O::add(O::sub(Xag, fa), Xagl), Yag), fa);
-      ob[2] = O::fma(om_a, O::sub(O::add(O::sub(Xag, fao), Xagl), Yag), fao);
-      oa[3] = O::fma(om_a, O::add(O::add(O::sub(Xal, fb), Xall), Yal), fb);
-      ob[3] = O::fma(om_a, O::sub(O::add(O::sub(Xal, fbo), Xall), Yal), fbo);
+      oa[0] = O::add(fg, O::fma(om_g, ta[0], O::add(Fg, Hg)));
+      ob[0] = O::add(fgo, O::fma(om_g, tb[0], O::sub(Fg, Hg)));
+      oa[1] = O::add(fl, O::fma(om_l, ta[1], O::add(Fl, Hl)));
+      ob[1] = O::add(flo, O::fma(om_l, tb[1], O::sub(Fl, Hl)));
+      oa[2] = O::fma(om_a, ta[2], fa);
+      ob[2] = O::fma(om_a, tb[2], fao);
+      oa[3] = O::fma(om_a, ta[3], fb);
+      ob[3] = O::fma(om_a, tb[3], fbo);
       if (!BS) {
         // beta_dev of q and opp(q) from one even part (v_opp . c = -v_q . c exactly)
         R vcg, vcl;
@@ -1235,6 +1251,7 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
       finish(qo, ob, INTc);
     }
   }
+  collide_rest(nsum, INTc);
   };
   if (interior) collide_all(std::true_type{});
   else collide_all(std::false_type{});
