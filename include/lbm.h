@@ -376,10 +376,14 @@ const char *lbm_fno_last_error(const lbm_fno *f);
 int lbm_fno_destroy(lbm_fno *f);
 /* The surrogate's matrix product alone (for tests and measurement):
  * C[b] = alpha op(A[b]) op(B[b]) + beta C[b], b < batch, BF16 A and B (device,
- * row-major; op(A) = A^T when ta, stored K x M), FP32 (out_f32) or BF16 C.
- * M, N, K multiples of 16, leading dimensions multiples of 8, pointers 32-byte
- * aligned.  ksplit > 1 splits K over blocks with FP32 atomics (needs out_f32
- * and beta = 1).  Enqueued on `stream`; LBM_EINVAL for bad shapes. */
+ * row-major; op(A) = A^T when ta, stored K x M), FP32 (out_f32) or BF16 C,
+ * on the tcgen05 tensor cores (FP32 accumulation in tensor memory, operands
+ * staged by TMA).  M, N, K multiples of 16, leading dimensions and batch
+ * strides multiples of 8 elements, pointers 32-byte aligned; a batch stride
+ * of 0 shares that operand across the batch (not for C when beta != 0).
+ * ksplit > 1 splits K over blocks with FP32 atomics (needs out_f32 and
+ * beta = 1).  Enqueued on `stream`; LBM_EINVAL for bad shapes (an operand
+ * the TMA unit cannot describe included). */
 int lbm_fno_gemm(int ta, int tb, int M, int N, int K, float alpha, const void *A, int lda, long long sA,
                  const void *B, int ldb, long long sB, float beta, void *C, int ldc, long long sC, int batch,
                  int out_f32, int ksplit, void *stream);

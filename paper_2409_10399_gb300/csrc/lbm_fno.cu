@@ -27,6 +27,7 @@
 
 #include "../../include/lbm.h"
 #include "fno_kernels.cuh"
+#include "fno_umma.cuh"
 #include "lbm_ctx_access.h"
 
 using fno::bf16;
@@ -106,8 +107,41 @@ static int ferr(lbm_fno *f, int code, const char *fmt, ...) {
 
 static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// After a synchronisation of the model's stream: a product whose pipeline
+// stalled (an mbarrier wait in k_umma ran out; its results are not valid)
+// is reported, and the flag cleared.
+static int umma_status(lbm_fno *f) {
+  int t = 0;
+  FTRY(f, cudaMemcpyFromSymbol(&t, fno::umma_timeout, sizeof t));
+  if (t) {
+    const int zero = 0;
+    FTRY(f, cudaMemcpyToSymbol(fno::umma_timeout, &zero, sizeof zero));
+    return ferr(f, LBM_ECUDA, "tensor-core product: a pipeline wait ran out (results invalid)");
+  }
+  return LBM_OK;
+}
+
 // ------------------------------------------------------------------ GEMM
 
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b], b < batch.  op(A) is M x K,
+// op(B) is K x N.  Row-major storage: A is M x K (lda >= K), or K x M
+// (lda >= M) when ta; B is K x N (ldb >= N), or N x K (ldb >= K) when tb;
+// C is M x N (ldc >= N), float or bf16.  M, N, K multiples of 16, leading
+// dimensions and batch strides multiples of 8, bases 32-byte aligned.
+// ksplit > 1 splits K into chunks (multiples of 64) over blocks, each adding
+// alpha times its partial product into a float C with atomics (C += alpha
+// op(A) op(B); beta must be 1).
+// With bias (float C, no split) the epilogue adds bias[b] (one value per
+// batch entry) or, with bias_rows, bias[row].  With hout it stores act ?
+// GELU(result) : result as bf16 at the same index of hout (the last product
+// of a surrogate layer, the lifting); C may then be null (beta 0), and the
+// float result is not stored; store_c = false keeps C as an input only.
+// The second segment (A2, batch 1, no split) adds a second product to the
+// same tile: C += A2_t B2_t over K2, where for output columns n (in rows of
+// seg_nx columns, seg_nx a multiple of 128) A2_t = A2 + (n / seg_nx) a2_rs is
+// K2 x M (lda2) and B2_t = B2 + (n % seg_nx) ldb2 is N x K2 (ldb2), both read
+// transposed: the pointwise product of a layer fused with the reconstruction
+// of its x spectrum, whose coefficients differ from row to row.
 struct G {
   const bf16 *A, *B;
   void *C;
@@ -120,15 +154,132 @@ struct G {
   const float *bias = nullptr;  // fused epilogue: + bias[batch] (bias[row] with bias_rows)
   bf16 *hout = nullptr;         // ... and (act ? GELU : identity) of the result as bf16; C may be null
   bool bias_rows = false, act = true, store_c = true;
-  // second product of the same tile (fno::GemmArgs, SEG2): pointwise + x reconstruction
+  // second product of the same tile: pointwise + x reconstruction
   const bf16 *A2 = nullptr, *B2 = nullptr;
   int K2 = 0, lda2 = 0, ldb2 = 0, seg_nx = 0;
   long long a2_rs = 0;
 };
 
-template <bool TA, bool TB, class OutT, bool SEG2 = false, bool PRE = false>
-static void launch_gemm_t(const fno::GemmArgs &a, dim3 grid, cudaStream_t st) {
-  fno::k_gemm<TA, TB, OutT, SEG2, PRE><<<grid, 128, 0, st>>>(a);
+// ---- tensor maps (cuTensorMapEncodeTiled, from the driver through the runtime's entry-point query)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// One operand as a 3D tensor (contiguous dimension `inner`, `rows` at
+// row_stride elements, `batch` at batch_stride elements), boxes of
+// box0 x box1; *bat says where the kernel puts the batch index (UmmaArgs).
+// A batch stride below the row stride is encoded with the outer dimensions
+// swapped, so that the map's strides grow outward.
+static cudaError_t operand_map(CUtensorMap *m, int *bat, const void *base, bool f32, long long inner, long long rows,
+                               int batch, long long row_stride, long long batch_stride, int box0, int box1, bool swz) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const long long es = f32 ? 4 : 2;
+  cuuint64_t dims[3];
+  cuuint64_t strides[2];
+  cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1}, estr[3] = {1, 1, 1};
+  if (batch <= 1 || batch_stride == 0) {
+    *bat = 0;
+    dims[0] = inner; dims[1] = rows; dims[2] = 1;
+    strides[0] = row_stride * es; strides[1] = rows * row_stride * es;
+  } else if (batch_stride >= row_stride) {
+    *bat = 1;
+    dims[0] = inner; dims[1] = rows; dims[2] = batch;
+    strides[0] = row_stride * es; strides[1] = batch_stride * es;
+  } else {
+    *bat = 2;
+    dims[0] = inner; dims[1] = batch; dims[2] = rows;
+    strides[0] = batch_stride * es; strides[1] = row_stride * es;
+    box[1] = 1; box[2] = (cuuint32_t)box1;
+  }
+  const CUresult r = enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                         const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 1;
+  }
+  return n;
+}
+
+// Buffers of one launch: three accumulators (with their old-C and staging
+// tiles) where shared memory allows, else two; a ring of two tiles' stages
+// (2 to 6); outputs through TMA stores when their staging tiles fit, else
+// stored directly.
+template <int NT, class OutT, bool OLDC>
+static int pick_smem(fno::UmmaArgs &a, int nk, bool want_c, bool want_h) {
+  typedef fno::UmmaSmem<NT, OutT, OLDC> SM;
+  const int limit = 227 * 1024;
+  const int stages = 2 * nk < 2 ? 2 : (2 * nk > 6 ? 6 : 2 * nk);
+  for (int st_out = 1; st_out >= 0; st_out--)
+    for (a.nacc = fno::UMMA_MAX_ACC; a.nacc >= 2; a.nacc--) {
+      a.st_c = st_out && want_c;
+      a.st_h = st_out && want_h;
+      for (a.stages = stages; a.stages >= 2; a.stages--) {
+        const int b = SM::bytes(a.stages, a.nacc, a.st_c, a.st_h);
+        if (b <= limit) {
+          a.tmem_cols = 32;
+          while (a.tmem_cols < a.nacc * NT) a.tmem_cols *= 2;
+          return b;
+        }
+      }
+    }
+  return -1;
+}
+
+template <bool AK, bool BKM, int NT, class OutT, bool SEG2, bool OLDC>
+static cudaError_t launch_umma(fno::UmmaArgs &a, int nk, bool want_c, bool want_h, cudaStream_t st) {
+  auto kern = fno::k_umma<AK, BKM, NT, OutT, SEG2, OLDC>;
+  const int smem = pick_smem<NT, OutT, OLDC>(a, nk, want_c, want_h);
+  if (smem < 0) return cudaErrorInvalidValue;
+  static int raised = 0;  // the kernel's dynamic shared-memory limit, raised once to the largest asked
+  if (smem > 48 * 1024 && smem > raised) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    raised = smem;
+  }
+  // persistent: as many blocks as fit on the GPU at once (and whose
+  // accumulators fit the 512 columns of an SM's tensor memory)
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, fno::UMMA_THREADS, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  if (per_sm > 512 / a.tmem_cols) per_sm = 512 / a.tmem_cols;
+  const long long cap = (long long)per_sm * num_sms();
+  const int grid = (int)(a.tiles < cap ? a.tiles : cap);
+  kern<<<grid, fno::UMMA_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool AK, bool BKM>
+static cudaError_t launch_umma_nt(fno::UmmaArgs &a, int nt, bool f32, bool oldc, int nk, bool want_c, bool want_h,
+                                  cudaStream_t st) {
+  if (oldc) return launch_umma<AK, BKM, 64, float, false, true>(a, nk, want_c, want_h, st);
+  if (f32) return nt == 64 ? launch_umma<AK, BKM, 64, float, false, false>(a, nk, want_c, want_h, st)
+                           : launch_umma<AK, BKM, 128, float, false, false>(a, nk, want_c, want_h, st);
+  return nt == 64 ? launch_umma<AK, BKM, 64, bf16, false, false>(a, nk, want_c, want_h, st)
+                  : launch_umma<AK, BKM, 128, bf16, false, false>(a, nk, want_c, want_h, st);
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
@@ -139,30 +290,65 @@ static cudaError_t gemm(const G &g, cudaStream_t st) {
   if (!g.C && (!g.hout || g.beta != 0.0f)) return cudaErrorInvalidValue;
   if (!g.store_c && (!g.hout || !g.C)) return cudaErrorInvalidValue;
   if (g.A2 && (!g.B2 || g.ta || g.tb || !g.out_f32 || g.batch != 1 || g.ksplit > 1 || g.K2 < 16 || g.K2 % 16 ||
-               g.lda2 % 8 || g.ldb2 % 8 || g.a2_rs % 8 || g.seg_nx < fno::GBN || g.seg_nx % fno::GBN ||
+               g.lda2 % 8 || g.ldb2 % 8 || g.a2_rs % 8 || g.seg_nx < fno::UMMA_M || g.seg_nx % fno::UMMA_M ||
                g.N % g.seg_nx || g.lda2 < g.M || g.ldb2 < g.K2 || (((uintptr_t)g.A2 | (uintptr_t)g.B2) & 31)))
     return cudaErrorInvalidValue;
   if (((uintptr_t)g.A | (uintptr_t)g.B | (uintptr_t)g.C) & 31) return cudaErrorMisalignedAddress;
   if (g.ksplit > 1 && !g.out_f32) return cudaErrorInvalidValue;
   int ks = g.ksplit < 1 ? 1 : g.ksplit;
-  int kchunk = ((g.K + ks - 1) / ks + fno::GBK - 1) / fno::GBK * fno::GBK;
+  int kchunk = ((g.K + ks - 1) / ks + fno::UMMA_BK - 1) / fno::UMMA_BK * fno::UMMA_BK;
   ks = (g.K + kchunk - 1) / kchunk;
   if ((long long)g.batch * ks > 65535) return cudaErrorInvalidValue;
-  fno::GemmArgs a{g.A, g.B, g.C, g.M, g.N, g.K, g.lda, g.ldb, g.ldc, g.sA, g.sB, g.sC, g.alpha, g.beta, ks, kchunk,
-                  g.bias, g.hout, g.bias_rows ? 1 : 0, g.act ? 1 : 0, g.store_c ? 1 : 0,
-                  g.A2, g.B2, g.K2, g.lda2, g.ldb2, g.seg_nx, g.a2_rs};
-  dim3 grid((g.N + fno::GBN - 1) / fno::GBN, (g.M + fno::GBM - 1) / fno::GBM, g.batch * ks);
-  const bool pre = g.out_f32 && g.beta != 0.0f && ks == 1;  // accumulate into C: prefetch the old tile
-  if (g.A2) launch_gemm_t<false, false, float, true>(a, grid, st);
-  else if (pre && g.ta && g.tb) launch_gemm_t<true, true, float, false, true>(a, grid, st);
-  else if (pre && g.ta) launch_gemm_t<true, false, float, false, true>(a, grid, st);
-  else if (pre && g.tb) launch_gemm_t<false, true, float, false, true>(a, grid, st);
-  else if (pre) launch_gemm_t<false, false, float, false, true>(a, grid, st);
-  else if (g.ta && g.tb) g.out_f32 ? launch_gemm_t<true, true, float>(a, grid, st) : launch_gemm_t<true, true, bf16>(a, grid, st);
-  else if (g.ta) g.out_f32 ? launch_gemm_t<true, false, float>(a, grid, st) : launch_gemm_t<true, false, bf16>(a, grid, st);
-  else if (g.tb) g.out_f32 ? launch_gemm_t<false, true, float>(a, grid, st) : launch_gemm_t<false, true, bf16>(a, grid, st);
-  else g.out_f32 ? launch_gemm_t<false, false, float>(a, grid, st) : launch_gemm_t<false, false, bf16>(a, grid, st);
-  return cudaGetLastError();
+  const bool oldc = g.out_f32 && g.beta != 0.0f && ks == 1;
+  if (oldc && g.batch > 1 && g.sC == 0) return cudaErrorInvalidValue;
+  const int nt = (oldc || g.M <= 64) ? 64 : 128;
+  fno::UmmaArgs a;
+  memset(&a, 0, sizeof a);
+  cudaError_t e;
+  // MMA A operand = op(B)^T: K-major when B is stored N x K (tb)
+  if (g.tb) e = operand_map(&a.ma, &a.a_bat, g.B, false, g.K, g.N, g.batch, g.ldb, g.sB, 64, fno::UMMA_M, true);
+  else e = operand_map(&a.ma, &a.a_bat, g.B, false, g.N, g.K, g.batch, g.ldb, g.sB, 64, 64, true);
+  if (e != cudaSuccess) return e;
+  // MMA B operand = op(A)^T: K-major when A is stored M x K (not ta)
+  if (!g.ta) e = operand_map(&a.mb, &a.b_bat, g.A, false, g.K, g.M, g.batch, g.lda, g.sA, 64, nt, true);
+  else e = operand_map(&a.mb, &a.b_bat, g.A, false, g.M, g.K, g.batch, g.lda, g.sA, 64, 64, true);
+  if (e != cudaSuccess) return e;
+  int unused;
+  if (g.A2) {
+    // second segment: B2 (seg_nx rows of K2, K-major) and the per-row tiles
+    // A2 + y a2_rs (K2 x M, MN-major), y over the N / seg_nx lattice rows
+    e = operand_map(&a.ma2, &unused, g.B2, false, g.K2, g.seg_nx, 1, g.ldb2, 0, 64, fno::UMMA_M, true);
+    if (e != cudaSuccess) return e;
+    if (g.a2_rs < (long long)g.K2 * g.lda2) return cudaErrorInvalidValue;
+    e = operand_map(&a.mb2, &unused, g.A2, false, g.M, g.K2, g.N / g.seg_nx, g.lda2, g.a2_rs, 64, 64, true);
+    if (e != cudaSuccess) return e;
+  }
+  // C's and hout's tiles (same layout): the old C tile is loaded through the
+  // map of C, and the output tiles leave through them when staged
+  const bool want_c = g.C && g.store_c && ks == 1, want_h = g.hout != nullptr;
+  if (g.C && (oldc || want_c)) {
+    e = operand_map(&a.mc, &a.c_bat, g.C, g.out_f32, g.N, g.M, g.batch, g.ldc, g.sC, fno::UMMA_M, nt, false);
+    if (e != cudaSuccess) return e;
+  }
+  if (want_h) {
+    e = operand_map(&a.mh, &a.c_bat, g.hout, false, g.N, g.M, g.batch, g.ldc, g.sC, fno::UMMA_M, nt, false);
+    if (e != cudaSuccess) return e;
+  }
+  a.C = g.C; a.M = g.M; a.N = g.N; a.K = g.K; a.ldc = g.ldc; a.sC = g.sC;
+  a.alpha = g.alpha; a.beta = g.beta; a.ksplit = ks; a.kchunk = kchunk;
+  a.bias = g.bias; a.hout = g.hout; a.bias_rows = g.bias_rows ? 1 : 0; a.act = g.act ? 1 : 0;
+  a.store_c = g.store_c ? 1 : 0; a.K2 = g.A2 ? g.K2 : 0; a.seg_nx = g.seg_nx;
+  a.tiles_n = (g.N + fno::UMMA_M - 1) / fno::UMMA_M;
+  a.tiles_m = (g.M + nt - 1) / nt;
+  const long long tiles = (long long)a.tiles_n * a.tiles_m * g.batch * ks;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  a.tiles = (int)tiles;
+  const int nk = (kchunk + fno::UMMA_BK - 1) / fno::UMMA_BK + (g.A2 ? (g.K2 + fno::UMMA_BK - 1) / fno::UMMA_BK : 0);
+  if (g.A2) return launch_umma<false, true, 64, float, true, false>(a, nk, want_c, want_h, st);
+  if (g.tb && !g.ta) return launch_umma_nt<true, true>(a, nt, g.out_f32, oldc, nk, want_c, want_h, st);
+  if (g.tb && g.ta) return launch_umma_nt<true, false>(a, nt, g.out_f32, oldc, nk, want_c, want_h, st);
+  if (!g.tb && !g.ta) return launch_umma_nt<false, true>(a, nt, g.out_f32, oldc, nk, want_c, want_h, st);
+  return launch_umma_nt<false, false>(a, nt, g.out_f32, oldc, nk, want_c, want_h, st);
 }
 
 // ------------------------------------------------------------------ kernels of the state interface
@@ -330,7 +516,7 @@ static int pointwise_and_spec_x(lbm_fno *f, const bf16 *W, const bf16 *h, bf16 *
   G w;  // z = W h (C x P)
   w.A = W; w.lda = C; w.B = h; w.ldb = (int)P; w.C = z; w.ldc = (int)P;
   w.M = C; w.N = (int)P; w.K = C;
-  if (nx % fno::GBN == 0) {
+  if (nx % fno::UMMA_M == 0) {
     // ... + for the tile of row y: O[y]^T (C x 2K) B_xi^T (2K x columns)
     w.A2 = f->O16; w.lda2 = C; w.a2_rs = (long long)K2 * C;
     w.B2 = f->Bxi; w.ldb2 = K2; w.K2 = K2; w.seg_nx = nx;
@@ -553,6 +739,7 @@ static int backward(lbm_fno *f, double *loss) {
   gi.M = C; gi.N = f->cin; gi.K = (int)P;
   GTRY(f, gi);
   FTRY(f, cudaStreamSynchronize(f->stream));
+  if (int rc = umma_status(f)) return rc;
   double s = 0.0;
   for (unsigned i = 0; i < nb; i++) s += f->h_part[i];
   double e0 = 0.0;
@@ -790,6 +977,7 @@ static int check_sums(lbm_fno *f, const double *now, const double *next, double 
   f->launches++;
   FTRY(f, cudaMemcpyAsync(f->h_red, f->red, 4 * blocks * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
   FTRY(f, cudaStreamSynchronize(f->stream));
+  if (int rc = umma_status(f)) return rc;
   for (int k = 0; k < 4; k++) {
     double t = 0.0;
     for (int i = 0; i < blocks; i++) t += f->h_red[k * blocks + i];

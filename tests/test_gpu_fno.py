@@ -1,14 +1,17 @@
 """GPU parity of the learned surrogate (lbm_fno_*) against the FP64 reference.
 
-- The BF16 matrix product (lbm_fno_gemm), every transpose combination, FP32
-  and BF16 outputs, batch strides, split-K, ragged sizes (multiples of 16),
-  against float64 products of the same BF16-rounded inputs: FP32 output
-  within 1e-5 relative (FP32 accumulation), BF16 output within 1e-2.
+- The BF16 matrix product (lbm_fno_gemm, tcgen05 with TMA-staged operands),
+  every transpose combination, FP32 and BF16 outputs, batch strides, split-K,
+  ragged sizes (multiples of 16), several tiles each way, more K stages than
+  the ring holds, an operand shared by the batch and one whose batch entries
+  interleave along its rows, against float64 products of the same
+  BF16-rounded inputs: FP32 output within 1e-5 relative (FP32
+  accumulation), BF16 output within 1e-2.
 - The surrogate step (lbm_fno_advance) against oracle/fno_ref.advance, the
   loss and the parameter gradient (lbm_fno_accumulate) against
   oracle/fno_ref.loss_and_grad (float64, FFT-based, autodiff pinned to finite
   differences) on a small model (32 x 48 nodes, C = 16, K = 8, L = 2: the
-  separate pointwise and x-reconstruction products) and a tall one (64 x 512,
+  separate pointwise and x-reconstruction products) and a tall one (128 x 512,
   L = 1: the two fused into one two-segment product, the y projections split
   over blocks).  The
   kernels round weights and activations to BF16 (8 significant bits), so the
@@ -28,7 +31,7 @@ from oracle import fno_ref
 pytestmark = pytest.mark.gpu
 
 DIMS = (32, 48, 16, 8, 2)  # nx, ny, C, K, L
-TALL = (64, 512, 16, 8, 1)  # nx % 64 == 0: pointwise + x reconstruction fused; ny >= 512: split y projection
+TALL = (128, 512, 16, 8, 1)  # nx % 128 == 0: pointwise + x reconstruction fused; ny >= 512: split y projection
 
 
 def _bf(t):
@@ -53,6 +56,42 @@ def test_gemm_against_float64(ta, tb, out):
         0.25 * C0.to(C.dtype).double()
     err = (C.double().cpu() - ref).norm() / ref.norm()
     assert err < (1e-5 if out == "f32" else 1e-2), err
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("beta,c_side", [(0.0, False), (0.5, False), (0.5, True)])
+def test_gemm_tiles_ring_and_batch_layouts(ta, tb, beta, c_side):
+    """M = 192 (one full and one partial tile of output rows), N = 336 (two
+    full and one partial tile of 128 columns), K = 320 (five 64-wide stages
+    through a ring of four), batch 2 with A shared by the batch (stride 0)
+    and B's batch entries side by side along its rows (batch stride below the
+    row stride); FP32 output, with and without the old C (beta), the old C
+    stacked by batch entry or side by side like B."""
+    g = torch.Generator(device="cpu").manual_seed(9)
+    M, N, K, batch = 192, 336, 320, 2
+    A = _bf(torch.randn((K, M) if ta else (M, K), generator=g)).cuda()
+    w = K if tb else N
+    Bbig = _bf(torch.randn((N if tb else K, batch * w), generator=g)).cuda()
+    C0 = torch.randn((batch, M, N), generator=g)
+    if c_side:
+        Cbig = torch.cat([C0[b] for b in range(batch)], dim=1).float().cuda()  # M x (batch N)
+        lbm.fno_gemm(A, Bbig, Cbig, ta=ta, tb=tb, alpha=0.5, beta=beta, batch=batch, sB=w, sC=N, M=M, N=N, K=K)
+        torch.cuda.synchronize()
+        got = [Cbig[:, b * N:(b + 1) * N] for b in range(batch)]
+    else:
+        C = C0.float().cuda()
+        lbm.fno_gemm(A, Bbig, C, ta=ta, tb=tb, alpha=0.5, beta=beta, batch=batch, sB=w, M=M, N=N, K=K)
+        torch.cuda.synchronize()
+        got = [C[b] for b in range(batch)]
+    a = A.double().cpu()
+    a = a.T if ta else a
+    err = 0.0
+    for b in range(batch):
+        bb = Bbig[:, b * w:(b + 1) * w].double().cpu()
+        ref = 0.5 * (a @ (bb.T if tb else bb)) + beta * C0[b].double()
+        err = max(err, ((got[b].double().cpu() - ref).norm() / ref.norm()).item())
+    assert err < 1e-5, err
 
 
 def test_gemm_split_k_and_strided_rows():
