@@ -346,15 +346,24 @@ int lbm_fno_accumulate(lbm_fno *f, const double *now, const double *next, double
  * sum(alpha_g), the quantity the volume check of lbm_fno_advance tests.
  * LBM_EINVAL for a negative or non-finite weight. */
 int lbm_fno_set_loss(lbm_fno *f, double cons_weight);
+/* Expected change dV of sum(alpha_g) over one model call (default 0, a
+ * closed box): the gas a lattice's inlet brings in during the window the
+ * call stands for.  The volume check of lbm_fno_advance (and so of
+ * lbm_surrogate_advance) then tests the change of each phase's volume
+ * against it: |(sum alpha_g' - sum alpha_g) - dV| relative to sum alpha_g
+ * and to sum (1 - alpha_g).  LBM_EINVAL for a non-finite dV.  Not in the
+ * paper. */
+int lbm_fno_set_inflow(lbm_fno *f, double dV);
 /* Adam step (Kingma & Ba, bias-corrected) with the accumulated gradients
  * times grad_scale, then gradients zeroed and the BF16 weights refreshed. */
 int lbm_fno_adam(lbm_fno *f, float lr, float beta1, float beta2, float eps, float grad_scale);
 /* Surrogate step: next = now + std_out * model(now) (device states, distinct
  * buffers).  *drift = relative change of the per-phase volumes sum(alpha_g)
- * and sum(1 - alpha_g) (the larger; infinite if any value of the new state
- * is not finite); *ok = drift <= max_drift and every new alpha_g in [0, 1].  Synchronises the stream (the
- * host reads the FP64 sums).  A caller that gets ok = 0 advances the state with the LBM
- * instead (the surrogate's fallback). */
+ * and sum(1 - alpha_g) beyond the expected inflow (lbm_fno_set_inflow; the
+ * larger of the two; infinite if any value of the new state is not finite);
+ * *ok = drift <= max_drift and every new alpha_g in [0, 1].  Synchronises the
+ * stream (the host reads the FP64 sums).  A caller that gets ok = 0
+ * advances the state with the LBM instead (the surrogate's fallback). */
 int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drift, double *drift, int *ok);
 /* One surrogate window on a live lattice: the surrogate's use with the LBM as
  * its fallback.  `ctx` must be a D2Q9 lattice of the model's nx x ny,

@@ -55,6 +55,17 @@ WORKLOADS = {
         physics=dict(_common_physics(), wall_friction=False, g_axis=1,
                      bc_lo=(PERIODIC, WALL, 0), bc_hi=(PERIODIC, WALL, 0)),
     ),
+    # surrogate workload with the 2D box's inlet: the box2d physics at 256 x
+    # 1024, its bottom strip scaled to width 64 (centred), injecting gas at
+    # fraction 0.3 and the box's full inlet velocity from the start (no
+    # ramp); walls on top, periodic x; initial gas plumes at random places
+    "surrogate2d_inlet": dict(
+        lattice="D2Q9", dims=(256, 1024, 1), steps=4096, precision="fp32",
+        physics=dict(_common_physics(), wall_friction=False, g_axis=1,
+                     bc_lo=(PERIODIC, INLET, 0), bc_hi=(PERIODIC, WALL, 0),
+                     inlet_lo=96, inlet_hi=160, in_alpha=(0.3, 0.3), in_ug=(4.3e-3, 4.3e-3),
+                     in_ul=(0.0, 0.0), inlet_ul_mode=1, ramp_nt=0),
+    ),
     # batched sweep: 256 independent D2Q9 columns (see batch_sweep), FP32
     "batch256": dict(lattice="D2Q9", dims=None, steps=10000, precision="fp32", physics=None),
     # 3D column, D3Q19, walls on the four x/y faces, periodic z, gravity along z.

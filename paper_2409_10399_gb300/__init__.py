@@ -94,6 +94,7 @@ def load_library(build_if_missing=True):
             "lbm_fno_set_stream": (I, [P, P]),
             "lbm_fno_accumulate": (I, [P, dp, dp, ctypes.POINTER(D)]),
             "lbm_fno_set_loss": (I, [P, D]),
+            "lbm_fno_set_inflow": (I, [P, D]),
             "lbm_fno_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
             "lbm_fno_advance": (I, [P, dp, dp, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "lbm_surrogate_advance": (I, [P, P, I, D, ctypes.POINTER(D), ctypes.POINTER(I)]),
@@ -488,6 +489,11 @@ class Surrogate:
     def set_loss(self, cons_weight):
         """Weight of the conservation term of the loss (lbm_fno_set_loss)."""
         self._check(self._lib.lbm_fno_set_loss(self._h, float(cons_weight)), "lbm_fno_set_loss")
+
+    def set_inflow(self, dV):
+        """Expected change of sum(alpha_g) over one call, the inlet's gas
+        (lbm_fno_set_inflow); the volume check tests the change beyond it."""
+        self._check(self._lib.lbm_fno_set_inflow(self._h, float(dV)), "lbm_fno_set_inflow")
 
     def accumulate(self, now, nxt):
         loss = ctypes.c_double()

@@ -78,6 +78,7 @@ struct lbm_fno {
   double *st = nullptr;  // FP64 states of lbm_surrogate_advance (now, next), allocated on first use
   double last_sums[4] = {0, 0, 0, 0};  // the check sums of the last lbm_fno_advance
   double cons = 0.0;                   // weight of the loss's conservation term
+  double inflow = 0.0;                 // expected change of sum(alpha_g) over one call
   float norm_mean[6] = {0, 0, 0, 0, 0, 0}, norm_std[6] = {1, 1, 1, 1, 1, 1}, out_std[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t stream = 0;
   long long launches = 0;
@@ -936,6 +937,12 @@ static Norm norm_of(const lbm_fno *f) {
   return nm;
 }
 
+int lbm_fno_set_inflow(lbm_fno *f, double dV) {
+  if (!f || !isfinite(dV)) return LBM_EINVAL;
+  f->inflow = dV;
+  return LBM_OK;
+}
+
 int lbm_fno_set_loss(lbm_fno *f, double cons_weight) {
   if (!f || !(cons_weight >= 0.0) || !isfinite(cons_weight)) return LBM_EINVAL;
   f->cons = cons_weight;
@@ -1044,15 +1051,17 @@ int lbm_fno_advance(lbm_fno *f, const double *now, double *next, double max_drif
       f->h16 + (long long)f->L * C * P, f->W_out16, f->p + f->off.b_out, now, next, C, P, nm);
   f->launches++;
   FTRY(f, cudaGetLastError());
-  // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g;
-  // a non-finite value anywhere in the new state, or a volume fraction
-  // outside [0, 1], fails the check too
+  // per-phase volume: sum alpha_g and sum (1 - alpha_g) = P - sum alpha_g,
+  // each changed by the expected inflow (the liquid's by minus it); a
+  // non-finite value anywhere in the new state, or a volume fraction outside
+  // [0, 1], fails the check too
   double sm[4];
   rc = check_sums(f, now, next, sm);
   if (rc) return rc;
   for (int k = 0; k < 4; k++) f->last_sums[k] = sm[k];
   const double g0 = sm[0], g1 = sm[1];
-  const double dg = fabs(g1 - g0) / fmax(g0, 1e-300), dl = fabs(g1 - g0) / fmax((double)P - g0, 1e-300);
+  const double ex = fabs((g1 - g0) - f->inflow);
+  const double dg = ex / fmax(g0, 1e-300), dl = ex / fmax((double)P - g0, 1e-300);
   const double d = isfinite(sm[2]) ? fmax(dg, dl) : INFINITY;
   if (drift) *drift = d;
   if (ok) *ok = d <= max_drift && sm[3] == 0.0;

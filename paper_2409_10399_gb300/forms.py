@@ -267,7 +267,7 @@ def surrogate(stream, reps=20):
     torch.cuda.synchronize()
     t_sur = e0.elapsed_time(e1) / 1e3 / reps
     m.close()
-    res = dict(workload="surrogate: D2Q9 256x1024 state, F-FNO C=64 K=32 L=4 (2,115,920 parameters), one call = "
+    res = dict(workload="surrogate: D2Q9 256x1024 inlet-box state, F-FNO C=64 K=32 L=4 (2,115,920 parameters), one call = "
                         "64 LBM steps", nodes=nx * ny, call_ms=t_sur * 1e3,
                tflops=S.model_flops(nx, ny, 64, 32, 4) / t_sur / 1e12)
     for prec in ("fp32", "fp64"):

@@ -2,19 +2,36 @@
 operator (lbm_fno_*) trained on trajectories of the library's own 2D LBM, that
 advances the state by 64 LBM steps per call, with the LBM as fallback.
 
-    python -m paper_2409_10399_gb300.surrogate [--train 96] [--test 8] [--epochs 16]
+    python -m paper_2409_10399_gb300.surrogate [--recipe inlet] [--train 2000] [--chunk 16]
 
-Workload (lbm_inputs "surrogate2d"): D2Q9 256 x 1024, FP32, R = 1000, the
-box2d physics in a closed box (periodic x, walls y), so that the per-phase
-volumes sum(alpha_g), sum(alpha_l) are conserved and the surrogate's mass
-check means something; initial states are gas plumes at random places
-(lbm_inputs.fields_plumes, seed per trajectory).  Each trajectory runs 4,096
-steps with a snapshot every 64: 64 (state, state 64 steps later) pairs.
+Workloads: D2Q9 256 x 1024, FP32, R = 1000, the box2d physics; initial
+states are gas plumes at random places (lbm_inputs.fields_plumes, seed per
+trajectory).  Each trajectory runs 4,096 steps with a snapshot every 64: 64
+(state, state 64 steps later) pairs.
+- `--recipe inlet` (lbm_inputs "surrogate2d_inlet", the default): the box's
+  bottom inlet strip (width 64, gas fraction 0.3 at the full inlet velocity)
+  and a top wall.  The per-phase volumes then grow with the inlet's gas, and
+  the mass check tests the change beyond an expected inflow
+  (lbm_fno_set_inflow): the nominal one, WINDOW x the strip's alpha_in u_in,
+  and the calibrated one, the mean change of sum(alpha_g) over the training
+  windows, which the check uses.  The LBM's own deviation from both is
+  measured on every training window and reported with the run; where it
+  exceeds the check's tolerance (--max-drift), the check cannot tell model
+  error from the method's own volume change, the run says so, and states
+  the fallback rate at the LBM's own floor (the 99th percentile of its
+  deviation) too, at which the hybrid run is made.
+- `--recipe plume` ("surrogate2d"): a closed box (periodic x, walls y), the
+  per-phase volumes conserved.
 
-Training: one sample per forward/backward (lbm_fno_accumulate), gradients
-averaged over a batch of samples, Adam with a cosine-decayed learning rate;
-the loss carries a conservation term of weight --cons (lbm_fno_set_loss) on
-the error of the window's change of sum(alpha_g).
+Training data are generated on the fly: `--chunk` trajectories at a time by
+the GPU LBM, their windows shuffled and trained on (`--epochs` passes),
+then freed, so that --train 2000 trajectories (128,000 windows, 1.6 TB in
+FP64 snapshots) never need to be stored; --chunk 0 keeps all of them and
+makes `--epochs` passes over the whole set.  One sample per forward/backward
+(lbm_fno_accumulate), gradients averaged over a batch of samples, Adam with a
+cosine-decayed learning rate; the loss carries a conservation term of weight
+--cons (lbm_fno_set_loss) on the error of the window's change of
+sum(alpha_g).
 Evaluation on held-out trajectories, per 64-step window and over rollouts of
 chained surrogate calls: relative L2 error of the predicted increment against
 the LBM's increment for each channel, of the state, the persistence baseline
@@ -40,11 +57,22 @@ from . import params as lparams
 
 WINDOW = 64
 CH = ("alpha_g", "u_gx", "u_gy", "u_lx", "u_ly", "p_k")
+RECIPES = {"inlet": "surrogate2d_inlet", "plume": "surrogate2d"}
 
 
-def _lbm_params(precision="fp32"):
-    w = lbm_inputs.WORKLOADS["surrogate2d"]
+def _lbm_params(precision="fp32", recipe="inlet"):
+    w = lbm_inputs.WORKLOADS[RECIPES[recipe]]
     return lparams.lattice_params(w["physics"], precision=precision)
+
+
+def inflow_per_window(recipe):
+    """The gas volume an inlet brings in over one window, WINDOW x the sum
+    over the inlet strip of alpha_in u_in (lattice units; the ramp-free
+    injection of the inlet recipe); 0 for a closed box."""
+    ph = lbm_inputs.WORKLOADS[RECIPES[recipe]]["physics"]
+    if ph["bc_lo"][ph["g_axis"]] != lbm_inputs.INLET:
+        return 0.0
+    return WINDOW * (ph["inlet_hi"] - ph["inlet_lo"]) * ph["in_alpha"][1] * ph["in_ug"][1]
 
 
 def _views(buf):
@@ -52,13 +80,13 @@ def _views(buf):
     return dict(alpha_g=buf[0], u_g=buf[1:3], u_l=buf[3:5], p_k=buf[5])
 
 
-def trajectories(n, seed0, nx, ny, steps):
+def trajectories(n, seed0, nx, ny, steps, recipe="inlet"):
     """(n, steps / 64 + 1, 6, nx*ny) float64 CUDA tensor of snapshots."""
     import torch
     P = nx * ny
     nsnap = steps // WINDOW + 1
     out = torch.empty((n, nsnap, 6, P), dtype=torch.float64, device="cuda")
-    p = _lbm_params()
+    p = _lbm_params(recipe=recipe)
     for i in range(n):
         s = Simulation("D2Q9", (nx, ny, 1), p)
         s.set_stream(torch.cuda.current_stream())
@@ -152,6 +180,89 @@ def train(model, data, epochs, batch=8, lr=2e-3, seed=0, log=None):
     return hist
 
 
+def window_volumes(data):
+    """The LBM's change of sum(alpha_g) over each window of `data` and the
+    gas volume at its start: two (trajectories, windows) float64 tensors."""
+    v = data[:, :, 0].sum(dim=2)
+    return v[:, 1:] - v[:, :-1], v[:, :-1]
+
+
+def inflow_deviation(dv, v, inflow):
+    """The change beyond an expected inflow, relative to the gas volume (the
+    quantity the volume check bounds)."""
+    return (dv - inflow).abs() / v
+
+
+def calibrate(dv, v, inflow, max_drift):
+    """The volume check's expected change per window: the nominal inflow,
+    and the mean change of the LBM's windows (dv, v: window_volumes,
+    flattened numpy arrays; calibrated, for a recipe with an inlet).  The
+    LBM's own spread about the calibrated value (its 99th percentile, the
+    floor) bounds from below the tolerances at which the check can tell
+    model error from the method's own change of sum(alpha_g).  Returns
+    (calibrated inflow, floor, a summary)."""
+    cal = float(dv.mean()) if inflow else 0.0
+    dn, dc = np.abs(dv - inflow) / v, np.abs(dv - cal) / v
+    floor = float(np.quantile(dc, 0.99))
+    return cal, floor, dict(windows=int(dv.size), lbm_dV_mean=float(dv.mean()), nominal_inflow=inflow,
+                            calibrated_inflow=cal,
+                            lbm_deviation_nominal=dict(median=float(np.median(dn)), p99=float(np.quantile(dn, 0.99)),
+                                                       max=float(dn.max())),
+                            lbm_deviation_calibrated=dict(median=float(np.median(dc)), p99=floor, max=float(dc.max())),
+                            check_separates_inflow=bool(dc.max() <= max_drift))
+
+
+def train_stream(model, n_traj, chunk, seed0, nx, ny, steps, recipe, epochs=1, batch=8, lr=2e-3, seed=0,
+                 on_first=None, log=None):
+    """Adam over the windows of n_traj trajectories generated `chunk` at a
+    time by the GPU LBM: each chunk's windows shuffled and used `epochs`
+    times, then freed; cosine learning-rate decay over the whole stream.
+    on_first(data) runs on the first chunk before any training (the
+    normalisation is fitted there).  Returns the mean loss per chunk, the
+    LBM's change of sum(alpha_g) and the gas volume at the start of every
+    window (window_volumes, flattened), and the seconds spent generating and
+    training."""
+    import torch
+    nsnap = steps // WINDOW + 1
+    nchunks = math.ceil(n_traj / chunk)
+    per_chunk = math.ceil(chunk * (nsnap - 1) / batch)
+    steps_total = max(1, nchunks * epochs * per_chunk)
+    r = np.random.default_rng(seed)
+    step, hist, dvs, vs = 0, [], [], []
+    t_gen = t_train = 0.0
+    for c in range(nchunks):
+        k = min(chunk, n_traj - c * chunk)
+        t0 = time.time()
+        data = trajectories(k, seed0 + c * chunk, nx, ny, steps, recipe)
+        dv, v = window_volumes(data)
+        dvs.append(dv.reshape(-1).cpu())
+        vs.append(v.reshape(-1).cpu())
+        t_gen += time.time() - t0
+        if c == 0 and on_first:
+            on_first(data)
+        t0 = time.time()
+        tot, cnt = 0.0, 0
+        for _ in range(epochs):
+            order = r.permutation(k * (nsnap - 1))
+            for b0 in range(0, len(order), batch):
+                idx = order[b0:b0 + batch]
+                for jj in idx:
+                    i, w = divmod(int(jj), nsnap - 1)
+                    tot += model.accumulate(data[i, w], data[i, w + 1])
+                    cnt += 1
+                lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * min(step, steps_total) / steps_total))
+                model.adam(lr_t, grad_scale=1.0 / len(idx))
+                step += 1
+        torch.cuda.synchronize()
+        t_train += time.time() - t0
+        hist.append(tot / max(1, cnt))
+        del data
+        if log and (c % 25 == 0 or c == nchunks - 1):
+            log(dict(chunk=c, trajectories_done=min(n_traj, (c + 1) * chunk), loss=hist[-1],
+                     gen_s=round(t_gen, 1), train_s=round(t_train, 1)))
+    return hist, torch.cat(dvs), torch.cat(vs), t_gen, t_train
+
+
 def _rel(a, b):
     nb = float(b.norm())
     return float((a - b).norm()) / nb if nb > 0 else float(a.norm())
@@ -200,7 +311,7 @@ def advance_with_fallback(model, sim, max_drift=1e-4):
     return used, d
 
 
-def hybrid(model, data, windows=8, max_drift=1e-4):
+def hybrid(model, data, windows=8, max_drift=1e-4, recipe="inlet"):
     """Live lattices advanced window by window through lbm_surrogate_advance
     (the surrogate, or 64 LBM steps when its check fails), judged against the
     plain LBM's snapshots of the same trajectories: alpha_g and state errors
@@ -217,7 +328,7 @@ def hybrid(model, data, windows=8, max_drift=1e-4):
     used_n, t_ms = 0, 0.0
     cur = torch.empty((6, P), dtype=torch.float64, device="cuda")
     for i in range(n):
-        sim = Simulation("D2Q9", (nx, ny, 1), _lbm_params())
+        sim = Simulation("D2Q9", (nx, ny, 1), _lbm_params(recipe=recipe))
         sim.set_stream(torch.cuda.current_stream())
         sim.init(**_views(data[i, 0]))
         for k in range(windows):
@@ -240,7 +351,7 @@ def hybrid(model, data, windows=8, max_drift=1e-4):
                 drift_max=float(np.max(drifts)), alpha_rel_l2=err_a.tolist(), state_rel_l2=err_s.tolist())
 
 
-def speed(model, state, nx, ny, reps=20):
+def speed(model, state, nx, ny, reps=20, recipe="inlet"):
     """Device time of a surrogate call and of 64 LBM steps on the same state."""
     import torch
     out = torch.empty_like(state)
@@ -253,7 +364,7 @@ def speed(model, state, nx, ny, reps=20):
     e1.record()
     torch.cuda.synchronize()
     t_sur = e0.elapsed_time(e1) / reps
-    s = Simulation("D2Q9", (nx, ny, 1), _lbm_params())
+    s = Simulation("D2Q9", (nx, ny, 1), _lbm_params(recipe=recipe))
     s.set_stream(torch.cuda.current_stream())
     s.init(**_views(state))
     s.step(WINDOW)
@@ -294,59 +405,109 @@ def model_flops(nx, ny, C, K, L):
 def main():
     import torch
     ap = argparse.ArgumentParser()
+    ap.add_argument("--recipe", choices=sorted(RECIPES), default="inlet")
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--ny", type=int, default=1024)
-    ap.add_argument("--train", type=int, default=96)
+    ap.add_argument("--train", type=int, default=2000, help="training trajectories")
+    ap.add_argument("--chunk", type=int, default=16,
+                    help="trajectories generated and trained on at a time (0: all stored, epochs over the set)")
     ap.add_argument("--test", type=int, default=8)
     ap.add_argument("--steps", type=int, default=4096)
-    ap.add_argument("--epochs", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=1, help="passes over each chunk (over the set with --chunk 0)")
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--cons", type=float, default=100.0,
                     help="weight of the loss's conservation term (lbm_fno_set_loss)")
+    ap.add_argument("--max-drift", type=float, default=1e-4, help="tolerance of the volume check")
     ap.add_argument("--channels", type=int, default=64)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--speed-only", action="store_true", help="time one surrogate call and 64 LBM steps, no training")
     ap.add_argument("--save", help="write the trained parameters and normalisation to this .npz")
     ap.add_argument("--load", help="skip training: parameters and normalisation from this .npz (from --save)")
+    ap.add_argument("--calib", type=int, default=32,
+                    help="trajectories that calibrate the expected inflow of a loaded model saved without it")
     args = ap.parse_args()
     emit = lambda d: print(json.dumps(d), flush=True)
+    inflow = inflow_per_window(args.recipe)
     if args.speed_only:
-        st = trajectories(1, 1000, args.nx, args.ny, WINDOW)[0, 1].contiguous()
+        st = trajectories(1, 1000, args.nx, args.ny, WINDOW, args.recipe)[0, 1].contiguous()
         m = Surrogate(args.nx, args.ny, args.channels, args.modes, args.layers)
         m.set_stream(torch.cuda.current_stream())
         m.set_params(init_params(args.channels, args.modes, args.layers))
-        emit(dict(stage="speed", nodes=args.nx * args.ny, **speed(m, st, args.nx, args.ny)))
+        emit(dict(stage="speed", nodes=args.nx * args.ny, **speed(m, st, args.nx, args.ny, recipe=args.recipe)))
         return
-    t0 = time.time()
-    train_data = trajectories(args.train, 1000, args.nx, args.ny, args.steps)
-    test_data = trajectories(args.test, 9000, args.nx, args.ny, args.steps)
-    emit(dict(stage="data", train_trajectories=args.train, test_trajectories=args.test,
-              pairs=args.train * (train_data.shape[1] - 1), wall_s=time.time() - t0))
     m = Surrogate(args.nx, args.ny, args.channels, args.modes, args.layers)
     m.set_stream(torch.cuda.current_stream())
+    m.set_loss(args.cons)
+    m.set_inflow(inflow)
+    t0 = time.time()
+    test_data = trajectories(args.test, 9000, args.nx, args.ny, args.steps, args.recipe)
+    emit(dict(stage="data", recipe=args.recipe, workload=RECIPES[args.recipe], train_trajectories=args.train,
+              test_trajectories=args.test, steps=args.steps, windows=args.train * (args.steps // WINDOW),
+              chunk=args.chunk, inflow_per_window=inflow, test_gen_s=time.time() - t0))
+    norm = {}
+
+    def set_norm(data):
+        norm["v"] = fit_norm(data)
+        m.set_norm(*norm["v"])
+
     if args.load:
         z = np.load(args.load)
-        params, (mean, std, dstd) = z["params"], (z["mean"], z["std"], z["dstd"])
+        m.set_params(z["params"])
+        norm["v"] = (z["mean"], z["std"], z["dstd"])
+        m.set_norm(*norm["v"])
+        if "inflow" in z:
+            inflow, norm["floor"] = float(z["inflow"]), float(z["floor"])
+        elif inflow:
+            # saved without its calibration: calibrate on fresh trajectories
+            cd = trajectories(args.calib, 5000, args.nx, args.ny, args.steps, args.recipe)
+            dv, v = (x.reshape(-1).cpu().numpy() for x in window_volumes(cd))
+            del cd
+            inflow, norm["floor"], summary = calibrate(dv, v, inflow, args.max_drift)
+            emit(dict(stage="calibrated", trajectories=args.calib, **summary))
+        m.set_inflow(inflow)
     else:
-        params = init_params(args.channels, args.modes, args.layers)
-        mean, std, dstd = fit_norm(train_data)
-    m.set_params(params)
-    m.set_norm(mean, std, dstd)
-    m.set_loss(args.cons)
-    emit(dict(stage="model", params=m.num_params, norm_mean=mean.tolist(), norm_std=std.tolist(),
-              increment_std=dstd.tolist(), loaded=bool(args.load), cons=args.cons))
-    if not args.load:
+        m.set_params(init_params(args.channels, args.modes, args.layers))
         t1 = time.time()
-        hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))
-        emit(dict(stage="trained", epochs=args.epochs, final_loss=hist[-1], wall_s=time.time() - t1))
+        if args.chunk <= 0 or args.chunk >= args.train:
+            train_data = trajectories(args.train, 1000, args.nx, args.ny, args.steps, args.recipe)
+            dv, v = (x.reshape(-1).cpu() for x in window_volumes(train_data))
+            set_norm(train_data)
+            hist = train(m, train_data, args.epochs, args.batch, args.lr, log=lambda d: emit(dict(stage="epoch", **d)))
+            del train_data
+            t_gen = t_train = None
+        else:
+            hist, dv, v, t_gen, t_train = train_stream(
+                m, args.train, args.chunk, 1000, args.nx, args.ny, args.steps, args.recipe, args.epochs, args.batch,
+                args.lr, on_first=set_norm, log=lambda d: emit(dict(stage="chunk", **d)))
+        # the check against the mean change of the training windows
+        inflow, norm["floor"], summary = calibrate(dv.numpy(), v.numpy(), inflow, args.max_drift)
+        m.set_inflow(inflow)
+        emit(dict(stage="trained", final_loss=hist[-1], wall_s=time.time() - t1, gen_s=t_gen, train_s=t_train,
+                  **summary))
+    mean, std, dstd = norm["v"]
+    emit(dict(stage="model", params=m.num_params, norm_mean=list(map(float, mean)), norm_std=list(map(float, std)),
+              increment_std=list(map(float, dstd)), loaded=bool(args.load), cons=args.cons))
     if args.save:
-        np.savez(args.save, params=m.params(), mean=mean, std=std, dstd=dstd)
-    ev = evaluate(m, test_data)
-    emit(dict(stage="test", **ev))
-    emit(dict(stage="hybrid", **hybrid(m, test_data)))
-    sp = speed(m, test_data[0, 0].contiguous(), args.nx, args.ny)
+        np.savez(args.save, params=m.params(), mean=mean, std=std, dstd=dstd, inflow=inflow,
+                 floor=norm.get("floor", 0.0))
+    ev = evaluate(m, test_data, max_drift=args.max_drift)
+    tdv, tv = window_volumes(test_data)
+    tdev = inflow_deviation(tdv, tv, inflow).reshape(-1).cpu().numpy()
+    # with a volume change the check cannot bound at --max-drift, the hybrid
+    # runs at the LBM's own floor (the p99 of its deviation on the training
+    # windows), and the fallback rate is stated at both tolerances
+    floor = norm.get("floor", 0.0)
+    tol = max(args.max_drift, floor)
+    extra = {}
+    if tol > args.max_drift:
+        extra = dict(floor_tolerance=tol, fallback_rate_at_floor=evaluate(m, test_data, max_drift=tol, rollout=0)[
+            "fallback_rate"])
+    emit(dict(stage="test", max_drift=args.max_drift, lbm_deviation_max=float(tdev.max()),
+              lbm_windows_failing_check=float((tdev > args.max_drift).mean()), **extra, **ev))
+    emit(dict(stage="hybrid", max_drift=tol, **hybrid(m, test_data, max_drift=tol, recipe=args.recipe)))
+    sp = speed(m, test_data[0, 0].contiguous(), args.nx, args.ny, recipe=args.recipe)
     # every failed check costs the surrogate call and then the 64 LBM steps
     t_eff = sp["surrogate_ms"] + ev["fallback_rate"] * sp["lbm_64_steps_ms"]
     emit(dict(stage="speed", nodes=args.nx * args.ny, effective_ms_with_fallback=t_eff,

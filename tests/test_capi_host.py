@@ -105,6 +105,7 @@ def test_surrogate_create_rejects_invalid_shapes_without_gpu():
         assert not h.value
     assert lib.lbm_fno_create(32, 32, 16, 8, 1, None) == -1
     assert lib.lbm_fno_set_loss(None, ctypes.c_double(1.0)) == -1
+    assert lib.lbm_fno_set_inflow(None, ctypes.c_double(1.0)) == -1
     assert lib.lbm_fno_advance(None, None, None, ctypes.c_double(1e-4), None, None) == -1
     assert lib.lbm_surrogate_advance(None, None, 64, ctypes.c_double(1e-4), None, None) == -1
     assert lib.lbm_fno_destroy(None) == 0

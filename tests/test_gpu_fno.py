@@ -159,6 +159,13 @@ def test_advance_against_reference(dims):
     assert ok == (expect <= 1.0)
     _, ok0 = m.advance(now_d, out, max_drift=0.0)
     assert not ok0  # any change of sum(alpha_g) fails a zero tolerance
+    # an expected inflow: the check tests the change beyond it
+    for dV in (s1 - s0, 0.5 * (s1 - s0) + 1.0):
+        m.set_inflow(dV)
+        d_in, _ = m.advance(now_d, out, max_drift=1.0)
+        ex = abs((s1 - s0) - dV)
+        assert abs(d_in - max(ex / s0, ex / (now.shape[1] - s0))) <= 1e-9 * max(ex / s0, 1e-30) + 1e-13
+    m.set_inflow(0.0)
     bad = now_d.clone()
     bad[3, 5] = float("nan")  # a liquid velocity, not alpha_g
     d_bad, ok_bad = m.advance(bad, out, max_drift=1e30)
@@ -214,7 +221,7 @@ def _lattice(dims=DIMS, seed=5, prec="fp64", **extra):
     import lbm_inputs
     from paper_2409_10399_gb300 import surrogate as S
     nx, ny = dims[0], dims[1]
-    sim = lbm.Simulation("D2Q9", (nx, ny), dict(S._lbm_params(prec), **extra))
+    sim = lbm.Simulation("D2Q9", (nx, ny), dict(S._lbm_params(prec, recipe="plume"), **extra))
     sim.init(**lbm_inputs.fields_plumes(nx, ny, seed))
     return sim
 

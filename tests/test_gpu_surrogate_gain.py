@@ -21,7 +21,7 @@ def test_trained_surrogate_beats_persistence():
     from paper_2409_10399_gb300 import surrogate as S
 
     nx, ny, C, K, L = 64, 128, 16, 8, 2
-    data = S.trajectories(3, 500, nx, ny, 64 * 8)  # 3 trajectories, 9 snapshots each
+    data = S.trajectories(3, 500, nx, ny, 64 * 8, recipe="plume")  # 3 trajectories, 9 snapshots each
     train, test = data[:2], data[2:]
     m = Surrogate(nx, ny, C, K, L)
     m.set_stream(torch.cuda.current_stream())
