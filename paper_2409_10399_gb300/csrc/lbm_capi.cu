@@ -323,12 +323,13 @@ static int choose_tiles(lbm_ctx *c) {
     c->smem = 0;
   }
   // beta-stencil form: the block's c tile plus a one-node halo, 2*D values
-  // per node in the held type, after the exchange area (16-byte aligned)
+  // per node padded to a multiple of 4 in the held type, after the exchange
+  // area (16-byte aligned)
   c->halo_off = 0;
   if (c->cfield || c->p.beta_stencil) {
     const size_t box = (size_t)(c->T[0] + 2) * (c->D > 1 ? c->T[1] + 2 : 1) * (c->D > 2 ? c->T[2] + 2 : 1);
     c->halo_off = (int)((c->smem + 15) / 16 * 16);
-    c->smem = (size_t)c->halo_off + box * 2 * c->D * held_size(c->prec);
+    c->smem = (size_t)c->halo_off + box * (size_t)((2 * c->D + 3) / 4 * 4) * held_size(c->prec);
   }
   if (c->smem > 227 * 1024) return set_err(c, LBM_EINVAL, "tile needs %zu bytes of shared memory (> 227 KB)", c->smem);
   for (int d = 0; d < 3; d++) c->grid[d] = (c->n[d] + c->shift[d] + c->T[d] - 1) / c->T[d];

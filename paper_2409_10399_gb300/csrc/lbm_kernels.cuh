@@ -366,7 +366,12 @@ __device__ __forceinline__ void beta_pair(int q, const R cg[3], const R cl[3], R
 // buffer 1 - parity) plus a one-node halo, staged once in shared memory, so
 // that the 2*D values of c at every x - v_q come from there instead of global
 // memory.  Node (lx, ly, lz) of the halo box is tile node (lx - 1, ly - 1,
-// lz - 1); components d of c_g at p[d*hn + k], of c_l at p[(D + d)*hn + k].
+// lz - 1); its values lie together, c_g then c_l, at p[k*HaloStride + ..]
+// (2*D padded to a multiple of 4 values: one or two 16-byte loads for FP32).
+template <class L>
+struct HaloStride {
+  static constexpr int v = (2 * L::D + 3) / 4 * 4;
+};
 struct CHalo {
   const void *p;  // nullptr: read c from global memory
   int hx, hy, hn;  // box extent along x, y; nodes in the box
@@ -376,11 +381,31 @@ struct CHalo {
 template <class L, class S, class R>
 __device__ __forceinline__ void halo_c(const CHalo &h, int k, R cg[3], R cl[3]) {
   typedef typename std::conditional<sizeof(S) == 8, double, float>::type H;
-  const H *p = (const H *)h.p;
+  constexpr int NV = HaloStride<L>::v;
+  H v[NV];
+  if constexpr (std::is_same<H, float>::value) {
+    const float4 *p = (const float4 *)h.p + (long long)k * (NV / 4);
+#pragma unroll
+    for (int j = 0; j < NV / 4; j++) {
+      const float4 t = p[j];
+      v[4 * j] = t.x;
+      v[4 * j + 1] = t.y;
+      v[4 * j + 2] = t.z;
+      v[4 * j + 3] = t.w;
+    }
+  } else {
+    const double2 *p = (const double2 *)h.p + (long long)k * (NV / 2);
+#pragma unroll
+    for (int j = 0; j < NV / 2; j++) {
+      const double2 t = p[j];
+      v[2 * j] = t.x;
+      v[2 * j + 1] = t.y;
+    }
+  }
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    cg[d] = d < L::D ? (R)p[d * h.hn + k] : R(0);
-    cl[d] = d < L::D ? (R)p[(L::D + d) * h.hn + k] : R(0);
+    cg[d] = d < L::D ? (R)v[d] : R(0);
+    cl[d] = d < L::D ? (R)v[L::D + d] : R(0);
   }
 }
 
@@ -417,7 +442,7 @@ __device__ __forceinline__ void stage_c_halo(const StepArgs &a, void *box, int h
       }
       const int k = r * hx + lx;
 #pragma unroll
-      for (int d = 0; d < 2 * L::D; d++) p[d * hn + k] = cb[d * a.plane + row + c0];
+      for (int d = 0; d < 2 * L::D; d++) p[k * HaloStride<L>::v + d] = cb[d * a.plane + row + c0];
     }
   }
 }
@@ -517,7 +542,29 @@ template <class L, class R, bool BS> struct Pops<L, __half, R, BS> {
 
 // Load all populations of the node with the AA read rule (INT: an interior
 // node, see read_slot), as raw values: deviations times Store<S>::scale.
-template <class L, class S, class R, bool BS = false, class OffT = long long, bool INT = false>
+// The beta populations of the beta-stencil form into the node's Pops (in
+// the store's raw units).
+template <class L, class S, class R, bool BS>
+__device__ __forceinline__ void load_node_beta(const StepArgs &a, const Geo &g, int parity, Pops<L, S, R, BS> &f,
+                                               const CHalo &h) {
+  if constexpr (!BS) return;
+  else if constexpr (std::is_same<S, MixAB>::value) {
+    load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
+  } else if constexpr (sizeof(S) == 2) {
+    load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
+#pragma unroll
+    for (int q = 0; q < L::Q; q++) {
+      f.fb[0][q] *= (R)Store<S>::scale;
+      f.fb[1][q] *= (R)Store<S>::scale;
+    }
+  } else {
+    load_beta<L, S, R>(a, g, parity, f.f[4], f.f[5], h);
+  }
+}
+
+// LB: the beta-stencil form's beta populations too (else the caller adds
+// them with load_node_beta, once the c halo is in shared memory).
+template <class L, class S, class R, bool BS = false, class OffT = long long, bool INT = false, bool LB = true>
 __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int parity, Pops<L, S, R, BS> &f,
                                           const CHalo &h = CHalo{nullptr, 0, 0, 0, 0}) {
   if constexpr (std::is_same<S, MixAB>::value) {
@@ -535,7 +582,6 @@ __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int p
 #pragma unroll
       for (int p = 0; p < (BS ? 1 : 2); p++) f.h[p][q] = __ldg(hb + p * Qp + off);
     }
-    if constexpr (BS) load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
   } else if constexpr (sizeof(S) == 2) {
     // half pairs: one 32-bit load per (pair, direction)
     const __half2 *pb[3];
@@ -548,14 +594,6 @@ __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int p
       const OffT off = pop_offset<L, OffT>(a, pq, idx);
 #pragma unroll
       for (int p = 0; p < (BS ? 2 : 3); p++) f.h[p][q] = __ldg(pb[p] + off);
-    }
-    if constexpr (BS) {
-      load_beta<L, S, R>(a, g, parity, f.fb[0], f.fb[1], h);
-#pragma unroll
-      for (int q = 0; q < L::Q; q++) {
-        f.fb[0][q] *= (R)Store<S>::scale;
-        f.fb[1][q] *= (R)Store<S>::scale;
-      }
     }
   } else {
     // the scheme bases formed once, before the loads (left inside the loop
@@ -571,8 +609,8 @@ __device__ __forceinline__ void load_node(const StepArgs &a, const Geo &g, int p
 #pragma unroll
       for (int s = 0; s < (BS ? 4 : 6); s++) f.f[s][q] = Store<S>::template ld_raw<R>(sb[s] + off);
     }
-    if (BS) load_beta<L, S, R>(a, g, parity, f.f[4], f.f[5], h);
   }
+  if constexpr (BS && LB) load_node_beta<L, S, R, BS>(a, g, parity, f, h);
 }
 
 // ------------------------------------------------------------- moments
@@ -833,10 +871,19 @@ template <> struct StepBounds<Lattice<1>, MixAB> { static constexpr int threads 
 // must call this function.
 // IO false: the lattice has no inlet or outlet face (walls and periodic axes
 // only), and the inlet/outlet rules are compiled out.
+// Beta-stencil form: where the block stages its c halo (k_step), filled by
+// fused_step_node once the node's own population loads are in flight.
+struct HaloStage {
+  void *box;       // nullptr: no staging (c from global memory)
+  int hx, hy, hn;  // box extent along x, y; nodes in the box
+  int o[3];        // the block's first tile node
+  int k;           // this thread's node in the box
+};
+
 template <class L, class S, class R, bool BS = false, class OffT = long long, bool IO = true>
 __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool active, int tid, int parity,
                                                 int latch, bool blk_xch, int gstride, R *xch,
-                                                const CHalo &halo = CHalo{nullptr, 0, 0, 0, 0}) {
+                                                const HaloStage &hs = HaloStage{nullptr, 0, 0, 0, {0, 0, 0}, 0}) {
   constexpr int D = L::D, Q = L::Q;
   const int gax = a.g_axis;
   Pops<L, S, R, BS> f;
@@ -855,9 +902,26 @@ __device__ __forceinline__ void fused_step_node(const StepArgs &a, Geo &g, bool 
     interior = !(g.xp[0] || g.xm[0] || g.xp[1] || g.xm[1] || g.xp[2] || g.xm[2]);
   }
   interior = SPLIT && __all_sync(__activemask(), interior);
+  if constexpr (BS) {
+    // the node's own populations first; the c halo is staged (and the block
+    // synchronised) while they are in flight, then the beta populations are
+    // evaluated from it
+    if (active) {
+      if (interior) load_node<L, S, R, BS, OffT, true, false>(a, g, parity, f);
+      else load_node<L, S, R, BS, OffT, false, false>(a, g, parity, f);
+    }
+    CHalo halo{nullptr, 0, 0, 0, 0};
+    if (hs.box) {
+      stage_c_halo<L, S>(a, hs.box, hs.hx, hs.hy, hs.hn, hs.o, tid, a.T[0] * a.T[1] * a.T[2]);
+      __syncthreads();
+      halo = CHalo{hs.box, hs.hx, hs.hy, hs.hn, hs.k};
+    }
+    if (active) load_node_beta<L, S, R, BS>(a, g, parity, f, halo);
+  } else if (active) {
+    if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f);
+    else load_node<L, S, R, BS, OffT>(a, g, parity, f);
+  }
   if (active) {
-    if (interior) load_node<L, S, R, BS, OffT, true>(a, g, parity, f, halo);
-    else load_node<L, S, R, BS, OffT>(a, g, parity, f, halo);
     moments<L, S, R, BS>(a, f, m);
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -1276,19 +1340,17 @@ __global__ void __launch_bounds__(StepBounds<L, S>::threads, StepBounds<L, S>::b
   const int sg = gax == 0 ? a.shift[0] : (gax == 1 ? a.shift[1] : a.shift[2]);
   const int blk_g0 = (int)(gax == 0 ? blockIdx.x : (gax == 1 ? blockIdx.y : blockIdx.z)) * Tg - sg;
   const bool blk_xch = IO && ((a.has_inlet && blk_g0 <= 0) || (a.has_outlet && blk_g0 + Tg >= ng));
-  CHalo halo{nullptr, 0, 0, 0, 0};
+  HaloStage hs{nullptr, 0, 0, 0, {0, 0, 0}, 0};
   if constexpr (BS) {
     // the block's c tile plus a one-node halo, from the last step's buffer
     const int hx = a.T[0] + 2, hy = L::D > 1 ? a.T[1] + 2 : 1, hz = L::D > 2 ? a.T[2] + 2 : 1;
-    const int o[3] = {(int)blockIdx.x * a.T[0] - a.shift[0], (int)blockIdx.y * a.T[1] - a.shift[1],
-                      (int)blockIdx.z * a.T[2] - a.shift[2]};
-    void *box = smem_raw + a.halo_off;
-    stage_c_halo<L, S>(a, box, hx, hy, hx * hy * hz, o, tid, a.T[0] * a.T[1] * a.T[2]);
-    __syncthreads();
-    const int k = (threadIdx.x + 1) + hx * ((L::D > 1 ? threadIdx.y + 1 : 0) + hy * (L::D > 2 ? threadIdx.z + 1 : 0));
-    halo = CHalo{box, hx, hy, hx * hy * hz, k};
+    hs = HaloStage{smem_raw + a.halo_off, hx, hy, hx * hy * hz,
+                   {(int)blockIdx.x * a.T[0] - a.shift[0], (int)blockIdx.y * a.T[1] - a.shift[1],
+                    (int)blockIdx.z * a.T[2] - a.shift[2]},
+                   (int)(threadIdx.x + 1) + hx * ((L::D > 1 ? (int)threadIdx.y + 1 : 0) +
+                                                  hy * (L::D > 2 ? (int)threadIdx.z + 1 : 0))};
   }
-  fused_step_node<L, S, R, BS, OffT, IO>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch, halo);
+  fused_step_node<L, S, R, BS, OffT, IO>(a, g, active, tid, a.parity, a.latch, blk_xch, gstride, xch, hs);
 }
 
 // Batched form: one launch advances many independent lattices (instances) of
