@@ -95,6 +95,20 @@ def batch_sweep(n=256, seed=4, side=(64, 512), R=(10.0, 1000.0), d_mm=(0.5, 5.0)
     return out
 
 
+def surrogate_inlet(seed, nx=256, width=64, alpha=(0.2, 0.4), u_scale=(0.5, 1.0)):
+    """Physics of one trajectory of the surrogate's inlet recipe: the
+    "surrogate2d_inlet" workload with its inlet varied by seed: the strip
+    (width `width`) at a uniform position along x, the injected gas fraction
+    uniform in `alpha`, the gas velocity the box's full inlet velocity times
+    a factor uniform in `u_scale`."""
+    r = rng(seed)
+    base = WORKLOADS["surrogate2d_inlet"]["physics"]
+    x0 = int(r.integers(0, nx - width + 1))
+    a_in = float(r.uniform(*alpha))
+    u_in = float(r.uniform(*u_scale)) * base["in_ug"][1]
+    return dict(base, inlet_lo=x0, inlet_hi=x0 + width, in_alpha=(a_in, a_in), in_ug=(u_in, u_in))
+
+
 def fields_step_profile(nx, ny, seed, low=0.9, high=0.1, noise=1e-3):
     """alpha_g = `low` below mid-height, `high` above, plus U(-noise, noise);
     at rest; p_k at the reference value."""
