@@ -11,7 +11,8 @@ the workload's stated step count (or at the reduced size the workload names
 for its error study), per field: alpha_g, u_g, u_l, p_k - 1/3.
 
 - box2d (D2Q9 512 x 2048, inlet strip, 20,000 steps): FP32 (the benchmark
-  form), FP16-dev, FP16AB, FP64.
+  form), FP16-dev, FP16AB, FP64, and the FP32 beta-stencil form (throughput,
+  with its fractions of the HBM peak on B_min and on B_6 separately).
 - column3d (D3Q19 256 x 256 x 512, 5,000 steps; errors at 64 x 64 x 128):
   FP16-dev (its form), FP16AB (f_g, f_l float), FP32, FP64.
 - batch256 (256 ragged D2Q9 FP32 columns, 1.06e8 nodes): one launch per step
@@ -147,6 +148,7 @@ def box2d(stream, quick=False):
     lat, dims = w["lattice"], w["dims"]
     res = dict(workload="box2d D2Q9 512x2048, R=1000, inlet strip", nodes=int(np.prod(dims)))
     res["forms"] = _lattice_forms("box2d", lat, dims, ("fp32", "fp16dev", "fp16ab", "fp64"), 400, stream)
+    res["forms"]["fp32_bstencil"] = bstencil_form("box2d", lat, dims, "fp32", 400, stream)
     steps = 2000 if quick else w["steps"]
     f = lbm_inputs.fields_for("box2d")
     ref, _ = run(lat, dims, lparams.lattice_params(w["physics"], precision="fp64"), f, steps, stream)
@@ -175,6 +177,40 @@ def column3d(stream, quick=False):
     res["accuracy"] = dict(against="fp64 GPU path, same state", steps=steps, dims=list(small), **acc)
     _speedups(res)
     return res
+
+
+# Beta-stencil form (Eq. (lbmbeta) with beta = 1, the beta schemes replaced
+# by the c field): bytes per node as stored (4 schemes' populations, the
+# held fields, the 2 D values of c read and written) and B_min, the same
+# without c; its fractions of the measured HBM peak are reported on B_min
+# and on B_6 (the six-scheme store it stands for) separately.
+BSTENCIL = {("D2Q9", "fp32"): (4 * 9 * 2 * 4 + 12 + 2 * 4 * 4, 300)}
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth (MEASURED_PEAKS.json at the repository
+    root), else the earlier GB300 measurement of 6,800 GB/s."""
+    import os
+    try:
+        with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def bstencil_form(name, lat, dims, prec, steps_time, stream):
+    w = lbm_inputs.WORKLOADS[name]
+    f = lbm_inputs.fields_for(name, dims=dims)
+    N = int(np.prod(dims))
+    s = _sim(lat, dims, dict(lparams.lattice_params(w["physics"], precision=prec), beta_stencil=1), f, stream)
+    sec = time_steps(s, steps_time, stream)
+    s.close()
+    stored, bmin = BSTENCIL[(lat, prec)]
+    peak = hbm_peak_gbs()
+    mlups = N / sec / 1e6
+    return dict(us_per_step=sec * 1e6, MLUPS=mlups, bytes_per_node=stored, GBs=N * stored / sec / 1e9,
+                timed_steps=steps_time, frac_of_peak_on_Bmin=mlups * 1e6 * bmin / 1e9 / peak,
+                frac_of_peak_on_B6=mlups * 1e6 * B6[(lat, prec)] / 1e9 / peak, B_min=bmin, B_6=B6[(lat, prec)])
 
 
 def _speedups(res):
