@@ -6,19 +6,21 @@ coupling, stabilisers, drag, forces, six collisions, AA streaming with the
 face rules) over the 2D bubble-column box: D2Q9, 512 x 2048 nodes, FP32 store
 and arithmetic, R = 1000, CGW drag, bottom inlet strip.  The library also
 enqueues its FP64 diagnostics after every DIAG_EVERY-th step; a timed run of K
-steps contains floor((t0 + K)/DIAG_EVERY) - floor(t0/DIAG_EVERY) of them (none
-for the default 20 steps after 5 warm-up steps), reported as
-`diag_passes_timed`.  The store (466 MB) is larger than L2, so no flush is
-needed between steps.
+steps after t0 warm-up steps contains floor((t0 + K)/DIAG_EVERY) -
+floor(t0/DIAG_EVERY) of them (200 for the default 20,000 steps after 100; none
+for 20 steps after 5), reported as `diag_passes_timed`; the kernel time of the
+roofline comes from the timed region's segments without them.  The store
+(466 MB) is larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
                   [--no-cpu-baseline] [--no-forms] [--quick-forms]
 
 Prints one JSON line.  Besides the benchmark's own keys it carries `forms`:
 every other form of the method timed live on the same GPU at its workload's
-full size (FP16-deviation store, FP64 reference path, the batched sweep, the
-learned surrogate, the 1D column), each with its speedup over the plain FP32
-and FP64 single-lattice paths and the accuracy it is run at
+full size (FP16-deviation and FP16AB stores, the beta-stencil form, FP64
+reference path, the batched sweep, the learned surrogate, the 1D column),
+each with its speedup over the plain FP32 and FP64 single-lattice paths and
+the accuracy it is run at
 (paper_2409_10399_gb300/forms.py).  Under torchrun (N > 1) every rank
 advances its own replica (different seed), timing is the max over ranks and
 `value` the aggregate; there is no data-path collective.
