@@ -284,7 +284,7 @@ static cudaError_t launch_umma_nt(fno::UmmaArgs &a, int nt, bool f32, bool oldc,
 }
 
 static cudaError_t gemm(const G &g, cudaStream_t st) {
-  if (g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1 || g.sA % 8 ||
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % 16 || g.N % 16 || g.K % 16 || g.lda % 8 || g.ldb % 8 || g.ldc % 8 || g.batch < 1 || g.sA % 8 ||
       g.sB % 8 || g.sC % 8)
     return cudaErrorInvalidValue;
   if ((g.bias || g.hout) && (!g.out_f32 || g.ksplit > 1 || ((uintptr_t)g.hout & 31))) return cudaErrorInvalidValue;

@@ -109,3 +109,13 @@ def test_surrogate_create_rejects_invalid_shapes_without_gpu():
     assert lib.lbm_fno_advance(None, None, None, ctypes.c_double(1e-4), None, None) == -1
     assert lib.lbm_surrogate_advance(None, None, 64, ctypes.c_double(1e-4), None, None) == -1
     assert lib.lbm_fno_destroy(None) == 0
+    # the product alone: shapes are checked before any device access (the
+    # addresses below are never dereferenced); empty or ragged (not a
+    # multiple of 16) sizes, leading dimensions not multiples of 8, a split
+    # K without beta = 1 are all LBM_EINVAL
+    a = ctypes.c_void_p(1 << 20)
+    f1, f0 = ctypes.c_float(1.0), ctypes.c_float(0.0)
+    for (M, N, K, lda, beta, ks) in [(0, 16, 16, 16, f0, 1), (16, 0, 16, 16, f0, 1), (16, 16, 0, 16, f0, 1),
+                                     (16, 16, 40, 48, f0, 1), (16, 16, 16, 12, f0, 1), (16, 16, 64, 64, f0, 2)]:
+        assert lib.lbm_fno_gemm(0, 0, M, N, K, f1, a, lda, 0, a, 16, 0, beta, a, 16, 0, 1, 1, ks, None) == -1, \
+            (M, N, K, lda, ks)
