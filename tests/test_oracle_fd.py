@@ -4,7 +4,9 @@ finite-difference solution of the same 1D Eulerian-Eulerian equations.
 * The FD solver's integrator (Dormand-Prince 5(4), the pair behind ode45) is
   pinned on ODEs with closed-form solutions.
 * The FD right-hand side reduces, for a uniform state, to the 0-D momentum
-  balance of Sec. 3.1 (buoyancy, drag, wall friction).
+  balance of Sec. 3.1 (buoyancy, drag, wall friction), and on single Fourier
+  modes to closed forms through the central differences' symbols
+  (advection, the gas continuity with its source, viscosity).
 * On a smooth periodic column (TEST #1 physics, sinusoidal alpha_g) the
   oracle LBM and the FD solution agree; the paper reports this agreement only
   qualitatively ("excellent"), so the bars are set from the O(eps^2)
@@ -42,6 +44,47 @@ def test_fd_rhs_homogeneous_limit():
     assert np.allclose(r[2 * N:3 * N], 1e-2 / (2.0 * 0.7) * abs(du) * (-du) - 2e-2 / (2.0 * 0.7) * abs(ul) * ul,
                        rtol=1e-12)
     assert np.allclose(r[3 * N:], 0.0, atol=1e-20)
+
+
+def test_fd_rhs_single_fourier_modes():
+    """Single Fourier modes on a periodic column, where the central
+    differences act through their symbols (Dx sin kx = sin k cos kx,
+    Dxx sin kx = -2 (1 - cos k) sin kx) and the right-hand side has a closed
+    form: (a) a volume-fraction wave carried by a uniform velocity of both
+    phases is advected, nothing else moves (no slip: no source, no drag, no
+    stress); (b) a gas velocity wave in a uniform mixture changes the
+    pressure through the gas continuity with its source, -cs2 alpha_g Dx u_g
+    (Eqs. (lbm-cont-g1DFD), (lbm-cont-g1D)), the gas momentum through
+    advection, viscosity and the source term S_g u_g, and the volume
+    fraction through -alpha_g Dx u_g."""
+    N, m, eps = 64, 3, 1e-3
+    k = 2 * np.pi * m / N
+    x = np.arange(N)
+    sn, cs = np.sin(k * x), np.cos(k * x)
+    p = dict(R=5.0, omega_g=0.7, omega_l=1.1, kappa_I=0.0, kappa_W=0.0, g_hat=0.0, drag_model=0)
+    s = fd.FD1D(N, p)
+    nu_g = 1.0 / 0.7 - 0.5
+    # (a) alpha_g = a0 + eps sin kx, u_g = u_l = U, p_k uniform
+    a0, U = 0.3, 2e-3
+    y = np.concatenate([np.full(N, 1 / 3), np.full(N, U), np.full(N, U), a0 + eps * sn])
+    r = s.rhs(0.0, y)
+    assert np.allclose(r[:N], 0.0, atol=1e-18)
+    assert np.allclose(r[N:3 * N], 0.0, atol=1e-18)
+    assert np.allclose(r[3 * N:], -U * eps * np.sin(k) * cs, rtol=1e-12, atol=1e-18)
+    # (b) u_g = eps sin kx, u_l = 0, alpha_g = a0, p_k uniform
+    y = np.concatenate([np.full(N, 1 / 3), eps * sn, np.zeros(N), np.full(N, a0)])
+    r = s.rhs(0.0, y)
+    al = 1.0 - a0
+    assert np.allclose(r[:N], -(1 / 3) * a0 * eps * np.sin(k) * cs, rtol=1e-12, atol=1e-20)
+    s2 = np.sin(2 * k * x)
+    want_ug = (-eps ** 2 * 0.5 * np.sin(2 * k) * s2          # -Dx(u_g^2), u_g^2 = eps^2 (1 - cos 2kx) / 2
+               - 2.0 * nu_g * (1.0 - np.cos(k)) * eps * sn   # nu_g Dxx u_g
+               + al * eps ** 2 * 0.5 * np.sin(k) * s2)       # S_g u_g, S_g = alpha_l eps sin k cos kx
+    assert np.allclose(r[N:2 * N], want_ug, rtol=1e-10, atol=1e-16)
+    # the liquid: its source S_l = Dx[alpha_g (u_l - u_g)] times u_l = 0, the pressure uniform, no drag
+    assert np.allclose(r[2 * N:3 * N], 0.0, atol=1e-20)
+    # the volume fraction carried by the gas wave, -Dx(alpha_g u_g) (Eq. (voidfraction1DFD))
+    assert np.allclose(r[3 * N:], -a0 * eps * np.sin(k) * cs, rtol=1e-12, atol=1e-18)
 
 
 @pytest.mark.parametrize("T,bars", [(2000, (1e-3, 2e-3, 1e-2, 1e-2)), (8000, (2e-3, 2e-3, 5e-3, 1e-2))])
