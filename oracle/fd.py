@@ -27,7 +27,10 @@ adaptive steps (the method behind ode45), written from its published
 coefficients; optional Gaussian moving-average smoothing of the solution every
 `smooth_every` accepted steps (Sec. 3.4; window 12, sigma = window/5).
 
-Parity: partial -- the paper reports FD/LBM agreement only qualitatively.
+Parity: the solver's parts are pinned (the integrator on closed-form ODEs,
+the right-hand side in the homogeneous limit and on single Fourier modes);
+its agreement with the LBM is a cross-check at a tolerance, since the paper
+reports that agreement only qualitatively.
 """
 import numpy as np
 
