@@ -14,8 +14,11 @@ from . import build as _build
 CACHE = os.path.join(_build.BUILD, "tiles.json")
 
 CANDIDATES = {
-    # (lattice, max threads): tiles
+    # (lattice dimension, the step kernel's largest block): tiles; every
+    # lattice and precision has an entry (the float and half kernels are
+    # built for 128 threads, the double ones for 256)
     (1, 128): [(128, 1, 1), (64, 1, 1), (96, 1, 1), (32, 1, 1)],
+    (1, 256): [(256, 1, 1), (128, 1, 1), (64, 1, 1), (32, 1, 1)],
     (2, 128): [(64, 2, 1), (32, 4, 1), (16, 8, 1), (128, 1, 1), (32, 2, 1), (64, 1, 1)],
     (2, 256): [(64, 4, 1), (32, 8, 1), (128, 2, 1), (64, 2, 1), (32, 4, 1)],
     (3, 256): [(32, 4, 2), (32, 2, 4), (64, 2, 2), (32, 8, 1), (16, 8, 2), (32, 4, 1)],
