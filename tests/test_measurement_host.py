@@ -68,3 +68,26 @@ def test_speedups():
     assert f["fp16dev"]["speedup_vs_fp32"] == pytest.approx(80 / 60) and f["fp16dev"]["speedup_vs_fp64"] == 40.0
     assert f["fp32"]["speedup_vs_fp64"] == 30.0 and "speedup_vs_fp32" not in f["fp32"]
     assert "speedup_vs_fp64" not in f["fp64"]
+
+
+def test_clock_sampler_parses_nvidia_smi_lines():
+    """The clock record of the timed region (nvidia-smi CSV, no units): the
+    median SM clock, the maximum, and every throttle reason seen active."""
+    s = bench.ClockSampler(0)
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s.proc = _Proc()
+    s.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2050, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 1980, 2070, 1400.0, 0x8, Active, Not Active, Not Active, Active",
+               "garbage", "0, N/A, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c = s.stop()
+    assert c == {"sm_mhz": 2050.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    empty = bench.ClockSampler(0)
+    assert empty.stop() is None
