@@ -119,3 +119,54 @@ def test_surrogate_create_rejects_invalid_shapes_without_gpu():
                                      (16, 16, 40, 48, f0, 1), (16, 16, 16, 12, f0, 1), (16, 16, 64, 64, f0, 2)]:
         assert lib.lbm_fno_gemm(0, 0, M, N, K, f1, a, lda, 0, a, 16, 0, beta, a, 16, 0, 1, 1, ks, None) == -1, \
             (M, N, K, lda, ks)
+
+
+def _set(p, **kv):
+    for k, v in kv.items():
+        if k in ("bc_lo", "bc_hi", "in_alpha", "in_ug", "in_ul"):
+            getattr(p, k)[:] = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("bad", [
+    dict(R=0.5), dict(omega_g=0.0), dict(omega_g=2.0), dict(omega_l=2.5), dict(omega_alpha=0.0),
+    dict(n_gamma=0), dict(spalding_mode=3), dict(spalding_mode=-1), dict(alpha_floor=0.0), dict(g_axis=2),
+    dict(g_axis=-1), dict(precision=5), dict(drag_model=2), dict(diag_every=-1), dict(beta_stencil=2),
+    dict(beta_stencil=1, precision=0), dict(R=float("nan")), dict(omega_g=float("nan")),
+    dict(bc_lo=[4, 1, 0], bc_hi=[4, 1, 0]),                      # unknown boundary code
+    dict(bc_lo=[0, 1, 0], bc_hi=[1, 1, 0]),                      # periodic on one face only
+    dict(bc_lo=[0, 1, 0], bc_hi=[0, 2, 0]),                      # inlet on the upper face
+    dict(bc_lo=[0, 3, 0], bc_hi=[0, 1, 0]),                      # outlet on the lower face
+    dict(bc_lo=[2, 1, 0], bc_hi=[1, 1, 0]),                      # inlet off the gravity axis
+    dict(bc_lo=[0, 2, 0], bc_hi=[0, 1, 0], inlet_ul_mode=1, in_alpha=[1.0, 1.0]),  # no liquid to balance
+])
+def test_create_rejects_invalid_parameters_without_gpu(bad):
+    """lbm_create checks every parameter before touching the device: each of
+    these single faults gives LBM_EINVAL and leaves the handle NULL (the
+    same parameters without the fault pass the checks: without a GPU they
+    fail only at the device allocation, LBM_ENOMEM)."""
+    lib = lbm.load_library()
+    ok = _set(lbm.default_params(), g_axis=1, bc_lo=[0, 1, 0], bc_hi=[0, 1, 0])
+    h0 = ctypes.c_void_p()
+    rc = lib.lbm_create(2, 2, 64, 32, 1, ctypes.byref(ok), ctypes.byref(h0))
+    assert rc in (0, -2), rc
+    if rc == 0:
+        lib.lbm_destroy(h0)
+    p = _set(lbm.default_params(), **dict(dict(g_axis=1, bc_lo=[0, 1, 0], bc_hi=[0, 1, 0]), **bad))
+    h = ctypes.c_void_p(12345)
+    assert lib.lbm_create(2, 2, 64, 32, 1, ctypes.byref(p), ctypes.byref(h)) == -1, bad
+    assert not h.value
+
+
+@pytest.mark.parametrize("dims", [(3, 2, 64, 32, 1), (2, 2, 64, 32, 2), (1, 1, 64, 2, 1), (2, 2, 0, 32, 1),
+                                  (2, 2, 1 << 16, 1 << 15, 1), (4, 4, 8, 8, 8)])
+def test_create_rejects_invalid_shapes_without_gpu(dims):
+    lib = lbm.load_library()
+    p = _set(lbm.default_params(), g_axis=0)
+    h = ctypes.c_void_p(12345)
+    assert lib.lbm_create(*dims, ctypes.byref(p), ctypes.byref(h)) == -1, dims
+    assert not h.value
+    assert lib.lbm_create(2, 2, 64, 32, 1, None, ctypes.byref(h)) == -1
+    assert lib.lbm_create(2, 2, 64, 32, 1, ctypes.byref(p), None) == -1
