@@ -170,3 +170,22 @@ def test_create_rejects_invalid_shapes_without_gpu(dims):
     assert not h.value
     assert lib.lbm_create(2, 2, 64, 32, 1, None, ctypes.byref(h)) == -1
     assert lib.lbm_create(2, 2, 64, 32, 1, ctypes.byref(p), None) == -1
+
+
+def test_batch_create_rejects_invalid_without_gpu():
+    """lbm_batch_create's checks that come before any device access: lattice
+    code, instance count, NULL arrays, the FP64 reference form (the batched
+    kernel runs the deviation forms), and an instance with an inlet, an
+    outlet or the beta-stencil form (the batched kernel has neither)."""
+    lib = lbm.load_library()
+    h = ctypes.c_void_p(12345)
+    dims = (ctypes.c_int * 3)(64, 32, 1)
+    base = dict(g_axis=1, bc_lo=[0, 1, 0], bc_hi=[0, 1, 0])
+    for lat, n, d, kv in [(4, 1, dims, {}), (2, 0, dims, {}), (2, 1, None, {}), (2, 1, dims, dict(precision=0)),
+                          (2, 1, dims, dict(bc_lo=[0, 2, 0])), (2, 1, dims, dict(bc_hi=[0, 3, 0])),
+                          (2, 1, dims, dict(beta_stencil=1))]:
+        p = _set(lbm.default_params(), **dict(base, **kv))
+        assert lib.lbm_batch_create(lat, n, d, ctypes.byref(p), ctypes.byref(h)) == -1, (lat, n, kv)
+        assert not h.value
+    assert lib.lbm_batch_create(2, 1, dims, None, ctypes.byref(h)) == -1
+    assert lib.lbm_batch_destroy(None) == 0
