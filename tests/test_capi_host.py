@@ -189,3 +189,31 @@ def test_batch_create_rejects_invalid_without_gpu():
         assert not h.value
     assert lib.lbm_batch_create(2, 1, dims, None, ctypes.byref(h)) == -1
     assert lib.lbm_batch_destroy(None) == 0
+
+
+def test_every_entry_point_rejects_null_handles():
+    """Every function include/lbm.h declares, called with NULL handles and
+    pointers and zero sizes (no GPU): LBM_EINVAL, except the NULL-safe
+    destroys (LBM_OK), the error-message accessors ("") and
+    lbm_default_params (nothing to fill)."""
+    lib = lbm.load_library()
+    for name in header_functions():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name  # every declared function has its signature in the binding
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_int, ctypes.c_longlong, ctypes.c_uint):
+                args.append(0)
+            elif t in (ctypes.c_double, ctypes.c_float):
+                args.append(0.0)
+            else:
+                args.append(None)
+        rc = fn(*args)
+        if name.endswith("_destroy"):
+            assert rc == 0, name
+        elif name.endswith("last_error"):
+            assert rc in (b"", None), name
+        elif name == "lbm_default_params":
+            assert rc is None
+        else:
+            assert rc == -1, (name, rc)
