@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -168,16 +169,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (a function-local static: thread-safe initialisation)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -215,13 +215,12 @@ static cudaError_t operand_map(CUtensorMap *m, int *bat, const void *base, bool 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// SMs of the current device
 static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 1;
-  }
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n < 1)
+    return 1;
   return n;
 }
 
@@ -255,11 +254,15 @@ static cudaError_t launch_umma(fno::UmmaArgs &a, int nk, bool want_c, bool want_
   auto kern = fno::k_umma<AK, BKM, NT, OutT, SEG2, OLDC>;
   const int smem = pick_smem<NT, OutT, OLDC>(a, nk, want_c, want_h);
   if (smem < 0) return cudaErrorInvalidValue;
-  static int raised = 0;  // the kernel's dynamic shared-memory limit, raised once to the largest asked
-  if (smem > 48 * 1024 && smem > raised) {
+  // the kernel's dynamic shared-memory limit, raised per device to the largest asked
+  static std::atomic<int> raised[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  std::atomic<int> &lim = raised[dev & 63];
+  if (smem > 48 * 1024 && smem > lim.load()) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    raised = smem;
+    lim.store(smem);
   }
   // persistent: as many blocks as fit on the GPU at once (and whose
   // accumulators fit the 512 columns of an SM's tensor memory)
